@@ -1,0 +1,191 @@
+/*
+ * gf2x_gb300.h -- C ABI of the GB300 (sm_103a) library for products of long
+ * binary polynomials with the additive FFT of Lin, Chung and Han over a tower
+ * field (Chen, Cheng, Kuo, Li, Yang, "Faster Multiplication for Long Binary
+ * Polynomials", arXiv:1708.09746).
+ *
+ * What is computed (Alg. 5 of the paper, binPolyMul): c(x) = a(x) * b(x) in
+ * GF(2)[x].  The library splits each operand into 64-bit blocks (Split,
+ * Sec. 2.1), converts them to the novelpoly basis (BasisCvt, Alg. 3),
+ * maps each block into the tower field F~_{2^128} (changeRepr, Sec. 4.3),
+ * evaluates both at N points with FFT_LCH (Alg. 1), multiplies pointwise
+ * (pointmul, Sec. 4.1.3), interpolates (iFFT_LCH), converts back (iBasisCvt,
+ * changeRepr^-1) and XOR-folds the overlapping 128-bit limbs
+ * (InterleavedCombine, Sec. 2.1).  Every step runs in CUDA kernels of this
+ * library; there is no CPU fallback: without a usable GPU every call returns
+ * GF2X_ECUDA.
+ *
+ * Conventions shared by every call:
+ *  - Polynomials are arrays of uint64_t words, little-endian: bit i of word j
+ *    is the coefficient of x^(64 j + i).  An n-bit operand occupies
+ *    ceil(n/64) words; bits at positions >= n are ignored on input.
+ *  - The product of an na-bit and an nb-bit operand has na+nb-1 bits and
+ *    occupies gf2x_out_words(na, nb) words; output bits at positions
+ *    >= na+nb-1 are written as 0.  A zero-length operand gives the empty
+ *    product (0 words written).
+ *  - Unless stated otherwise, data pointers are DEVICE pointers (cudaMalloc,
+ *    cudaMallocAsync or PyTorch CUDA tensors) on the current device.  A host
+ *    pointer gives GF2X_EINVAL.  The caller owns all buffers and keeps them
+ *    alive until the call (or its stream) completes.
+ *  - `out` must not overlap `a` or `b` (GF2X_EINVAL).
+ *  - Asynchronous calls enqueue kernels on the caller's stream (0 = the
+ *    legacy default stream) and return without waiting.
+ *  - Every call returns an int status; no C++ exception crosses this ABI.
+ *  - Sizes: operands up to 2^33 bits each (N <= 2^28 FFT points); larger
+ *    sizes give GF2X_EINVAL.
+ */
+#ifndef GF2X_GB300_H
+#define GF2X_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GF2X_API __attribute__((visibility("default")))
+#else
+#define GF2X_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *gf2x_stream_t; /* same handle as cudaStream_t */
+
+enum {
+    GF2X_OK = 0,
+    GF2X_EINVAL = -1,   /* bad argument (size, null, host pointer, overlap) */
+    GF2X_ENOMEM = -2,   /* device or host allocation failed */
+    GF2X_ECUDA = -3,    /* a CUDA call or kernel launch failed, or no GPU */
+    GF2X_ETIMEOUT = -4, /* a bounded wait ran out (server API) */
+    GF2X_EBUSY = -5     /* a resource is in use (server slots / budget) */
+};
+
+/* Human-readable text for a status code.  Never NULL. */
+GF2X_API const char *gf2x_strerror(int status);
+
+/* Words of the product of an na-bit and an nb-bit operand:
+ * ceil((na+nb-1)/64), or 0 if either size is 0. */
+GF2X_API uint64_t gf2x_out_words(uint64_t na_bits, uint64_t nb_bits);
+
+/* Number of FFT points N the library uses for these operand sizes: the
+ * smallest power of two >= na_w + nb_w - 1 (at least 2), na_w = ceil(na/64).
+ * 0 if either size is 0. */
+GF2X_API uint64_t gf2x_fft_points(uint64_t na_bits, uint64_t nb_bits);
+
+/* ---- One-shot products ---------------------------------------------------*/
+
+/* c = a * b (Alg. 5).  Synchronous: enqueues on the legacy default stream,
+ * allocates its workspace there (stream-ordered) and waits for completion. */
+GF2X_API int gf2x_mul(const uint64_t *a, uint64_t na_bits, const uint64_t *b,
+             uint64_t nb_bits, uint64_t *out);
+
+/* As gf2x_mul, asynchronous on `stream`.  The workspace is allocated and
+ * freed stream-ordered on `stream`. */
+GF2X_API int gf2x_mul_async(const uint64_t *a, uint64_t na_bits, const uint64_t *b,
+                   uint64_t nb_bits, uint64_t *out, gf2x_stream_t stream);
+
+/* As gf2x_mul with HOST buffers a, b, out (pageable or pinned).  The call
+ * copies the operands to the device, runs the product and copies the result
+ * back, all on `stream`, and returns after the result is in `out`. */
+GF2X_API int gf2x_mul_host(const uint64_t *a_host, uint64_t na_bits,
+                  const uint64_t *b_host, uint64_t nb_bits, uint64_t *out_host,
+                  gf2x_stream_t stream);
+
+/* ---- Plans (per-size tables and pass schedule, device resident) ---------*/
+
+typedef struct gf2x_plan gf2x_plan; /* opaque, library-owned */
+
+/* Builds the plan for operands of exactly na_bits and nb_bits: the pass
+ * schedule of BasisCvt/FFT, the butterfly multiplier tables s_k(alpha)
+ * (Sec. 4.4) and the changeRepr tables (Sec. 4.3), uploaded to the current
+ * device.  *p receives the plan; free it with gf2x_plan_destroy. */
+GF2X_API int gf2x_plan_create(uint64_t na_bits, uint64_t nb_bits, gf2x_plan **p);
+
+/* Device workspace in bytes that gf2x_plan_execute needs (2 x 16 N bytes of
+ * FFT arrays plus the padded operands). */
+GF2X_API int gf2x_plan_workspace_bytes(const gf2x_plan *p, size_t *bytes);
+
+/* Runs the product with plan p on `stream`.  workspace: a device buffer of at
+ * least gf2x_plan_workspace_bytes bytes, 256-byte aligned, or NULL to use a
+ * buffer the plan owns (allocated on first use; executions that share it are
+ * then serialised by the caller's stream order).  Asynchronous. */
+GF2X_API int gf2x_plan_execute(gf2x_plan *p, const uint64_t *a, const uint64_t *b,
+                      uint64_t *out, void *workspace, gf2x_stream_t stream);
+
+GF2X_API int gf2x_plan_destroy(gf2x_plan *p);
+
+/* ---- Batched products -----------------------------------------------------*/
+
+/* count independent products out[i] = a[i] * b[i], of any (uneven) sizes,
+ * enqueued on `stream`.  The arrays a, na_bits, b, nb_bits, out are HOST
+ * arrays of `count` entries; a[i], b[i], out[i] are device pointers.  Plans
+ * per size are cached and reused; workspaces come from one pooled device
+ * allocation.  Asynchronous. */
+GF2X_API int gf2x_mul_batched(int count, const uint64_t *const *a,
+                     const uint64_t *na_bits, const uint64_t *const *b,
+                     const uint64_t *nb_bits, uint64_t *const *out,
+                     gf2x_stream_t stream);
+
+/* ---- Stage entry points (each one row of the method, for checking and
+ * profiling one stage alone; all device pointers, asynchronous) ----------*/
+
+/* BasisCvt (Alg. 3, Appendix B) in place on 2^log_n 64-bit coefficients
+ * (inverse = 0) or its inverse iBasisCvt (inverse = 1). */
+GF2X_API int gf2x_stage_basis_cvt64(uint64_t *f, int log_n, int inverse,
+                           gf2x_stream_t stream);
+
+/* The same on 2^log_n 128-bit coefficients stored as (lo, hi) word pairs. */
+GF2X_API int gf2x_stage_basis_cvt128(uint64_t *f, int log_n, int inverse,
+                            gf2x_stream_t stream);
+
+/* changeRepr (Sec. 4.3): F[i] = phi(g[i mod p]) for i < n, where phi maps a
+ * 64-bit block p(z) to p(r) in F~_{2^128}; F holds n (lo, hi) pairs.  The
+ * periodic copy is the fan-out of the FFT layers above log2(p) (Fig. 2). */
+GF2X_API int gf2x_stage_chrepr(const uint64_t *g, uint64_t p, uint64_t *F, uint64_t n,
+                      gf2x_stream_t stream);
+
+/* FFT_LCH (Alg. 1) in place on 2^log_n elements (lo, hi pairs) at the points
+ * \bar{i}, i < 2^log_n; only layers k < log_p are computed (the layers above
+ * are fan-outs, already applied by gf2x_stage_chrepr).  inverse = 1 runs
+ * iFFT_LCH over all layers (log_p ignored). */
+GF2X_API int gf2x_stage_fft(uint64_t *F, int log_n, int log_p, int inverse,
+                   gf2x_stream_t stream);
+
+/* pointmul: C[i] = A[i] * B[i] in F~_{2^128} for i < n (C may equal B). */
+GF2X_API int gf2x_stage_pointmul(const uint64_t *A, const uint64_t *B, uint64_t *C,
+                        uint64_t n, gf2x_stream_t stream);
+
+/* changeRepr^-1 and InterleavedCombine: out[j] = lo(psi(F[j])) ^
+ * hi(psi(F[j-1])) for j < ceil(total_bits/64), bits >= total_bits cleared;
+ * F holds n (lo, hi) pairs (entries past n read as 0). */
+GF2X_API int gf2x_stage_ichrepr_combine(const uint64_t *F, uint64_t n, uint64_t *out,
+                               uint64_t total_bits, gf2x_stream_t stream);
+
+/* ---- Per-stage timing (the component profile of the paper's Table 4) ----*/
+
+/* on = 1: every later product records a CUDA event before and after each of
+ * its stages (split, basis_cvt, chrepr, fft, pointmul, ifft, ibasis_cvt,
+ * ichrepr_combine) on the stream it runs on.  on = 0 stops recording. */
+GF2X_API int gf2x_profile_enable(int on);
+
+/* Drops recorded events and zeroes the sums. */
+GF2X_API int gf2x_profile_reset(void);
+
+/* Waits for the recorded events, then returns for stage index `stage`
+ * (0 .. 7, order above) the summed elapsed milliseconds, the number of
+ * kernel launches in those stages and the number of stage executions. */
+GF2X_API int gf2x_profile_read(int stage, double *ms, uint64_t *launches,
+                               uint64_t *calls);
+
+/* Name of stage index `stage`, or "" if out of range. */
+GF2X_API const char *gf2x_profile_stage_name(int stage);
+
+/* Releases the per-device tables and cached plans of this library. */
+GF2X_API int gf2x_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GF2X_GB300_H */

@@ -195,3 +195,29 @@ int gf2o_num_threads(void)
     return 1;
 #endif
 }
+
+/* Word j of the product a*b straight from the definition: the words a_i and
+ * b_{j-i} meet at word j through the low half of their carry-less product
+ * and a_i, b_{j-1-i} through the high half.  O(min(na, nb)) per word; used
+ * to check sampled words of products too long for a full oracle run.
+ * Operands must already have their bits past the length cleared. */
+uint64_t gf2o_product_word(const uint64_t *a, int64_t na, const uint64_t *b,
+                           int64_t nb, int64_t j)
+{
+    uint64_t acc = 0;
+    int64_t i0 = j - (nb - 1);
+    if (i0 < 0) i0 = 0;
+    for (int64_t i = i0; i <= j && i < na; i++) {
+        uint64_t lo, hi;
+        gf2o_clmul64(a[i], b[j - i], &lo, &hi);
+        acc ^= lo;
+    }
+    i0 = j - 1 - (nb - 1);
+    if (i0 < 0) i0 = 0;
+    for (int64_t i = i0; i <= j - 1 && i < na; i++) {
+        uint64_t lo, hi;
+        gf2o_clmul64(a[i], b[j - 1 - i], &lo, &hi);
+        acc ^= hi;
+    }
+    return acc;
+}

@@ -35,6 +35,9 @@ def lib():
                                     ctypes.c_uint64]
         L.gf2o_mulmod64.restype = ctypes.c_uint64
         L.gf2o_num_threads.restype = ctypes.c_int
+        L.gf2o_product_word.argtypes = [u64p, ctypes.c_int64, u64p, ctypes.c_int64,
+                                        ctypes.c_int64]
+        L.gf2o_product_word.restype = ctypes.c_uint64
         _lib = L
     return _lib
 
@@ -110,6 +113,13 @@ def mul(a, na_bits, b, nb_bits, threads=None):
     if threads > 1 and nw >= 4096:
         depth = 2 if threads < 16 else 3
     return mul_karatsuba(a, na_bits, b, nb_bits, par_depth=depth)
+
+
+def product_word(a, na_bits, b, nb_bits, j):
+    """Word j of a*b from the definition (for sampled checks of long
+    products).  The caller masks bits >= total length in the last word."""
+    A, B = _words(a, na_bits), _words(b, nb_bits)
+    return int(lib().gf2o_product_word(_p(A), len(A), _p(B), len(B), int(j)))
 
 
 def poly_mod64(a, nbits, r_low):

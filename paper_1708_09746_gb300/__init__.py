@@ -1,0 +1,235 @@
+"""Python binding of libgf2x_gb300 (include/gf2x_gb300.h).
+
+Argument marshalling only: every step of the product runs in the CUDA kernels
+of the shared library; nothing here computes.  The functions carry the C ABI's
+names and arguments.  Device buffers are passed as PyTorch CUDA tensors (any
+integer dtype; their bytes are the little-endian uint64 words), host buffers
+as numpy arrays, streams as torch.cuda.Stream (or None for the legacy default
+stream).  A non-zero status raises GF2XError.
+
+The library must be built first (paper_1708_09746_gb300.build); loading fails
+loudly if it is missing -- there is no fallback implementation.
+"""
+import ctypes
+import os
+
+__all__ = [
+    "GF2XError", "load", "gf2x_strerror", "gf2x_out_words", "gf2x_fft_points",
+    "gf2x_mul", "gf2x_mul_async", "gf2x_mul_host", "gf2x_plan_create",
+    "gf2x_plan_workspace_bytes", "gf2x_plan_execute", "gf2x_plan_destroy",
+    "gf2x_mul_batched", "gf2x_stage_basis_cvt64", "gf2x_stage_basis_cvt128",
+    "gf2x_stage_chrepr", "gf2x_stage_fft", "gf2x_stage_pointmul",
+    "gf2x_stage_ichrepr_combine", "gf2x_shutdown", "gf2x_profile_enable",
+    "gf2x_profile_reset", "gf2x_profile_read", "gf2x_profile_stage_name", "LIB_PATH",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libgf2x_gb300.so")
+
+GF2X_OK, GF2X_EINVAL, GF2X_ENOMEM, GF2X_ECUDA, GF2X_ETIMEOUT, GF2X_EBUSY = 0, -1, -2, -3, -4, -5
+
+
+class GF2XError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (where, gf2x_strerror(status), status))
+
+
+_lib = None
+_u64 = ctypes.c_uint64
+_vp = ctypes.c_void_p
+_int = ctypes.c_int
+
+_SIGS = {
+    "gf2x_strerror": (ctypes.c_char_p, [_int]),
+    "gf2x_out_words": (_u64, [_u64, _u64]),
+    "gf2x_fft_points": (_u64, [_u64, _u64]),
+    "gf2x_mul": (_int, [_vp, _u64, _vp, _u64, _vp]),
+    "gf2x_mul_async": (_int, [_vp, _u64, _vp, _u64, _vp, _vp]),
+    "gf2x_mul_host": (_int, [_vp, _u64, _vp, _u64, _vp, _vp]),
+    "gf2x_plan_create": (_int, [_u64, _u64, ctypes.POINTER(_vp)]),
+    "gf2x_plan_workspace_bytes": (_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "gf2x_plan_execute": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "gf2x_plan_destroy": (_int, [_vp]),
+    "gf2x_mul_batched": (_int, [_int, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "gf2x_stage_basis_cvt64": (_int, [_vp, _int, _int, _vp]),
+    "gf2x_stage_basis_cvt128": (_int, [_vp, _int, _int, _vp]),
+    "gf2x_stage_chrepr": (_int, [_vp, _u64, _vp, _u64, _vp]),
+    "gf2x_stage_fft": (_int, [_vp, _int, _int, _int, _vp]),
+    "gf2x_stage_pointmul": (_int, [_vp, _vp, _vp, _u64, _vp]),
+    "gf2x_stage_ichrepr_combine": (_int, [_vp, _u64, _vp, _u64, _vp]),
+    "gf2x_shutdown": (_int, []),
+    "gf2x_profile_enable": (_int, [_int]),
+    "gf2x_profile_reset": (_int, []),
+    "gf2x_profile_read": (_int, [_int, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+    "gf2x_profile_stage_name": (ctypes.c_char_p, [_int]),
+}
+
+
+def load():
+    """Load the shared library (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError("libgf2x_gb300.so is not built (run "
+                          "`python -m paper_1708_09746_gb300.build`): " + LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Raw address of a torch tensor / numpy array / int (None -> 0)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(rc, where):
+    if rc != GF2X_OK:
+        raise GF2XError(rc, where)
+
+
+def gf2x_strerror(status):
+    return load().gf2x_strerror(int(status)).decode()
+
+
+def gf2x_out_words(na_bits, nb_bits):
+    return int(load().gf2x_out_words(na_bits, nb_bits))
+
+
+def gf2x_fft_points(na_bits, nb_bits):
+    return int(load().gf2x_fft_points(na_bits, nb_bits))
+
+
+def gf2x_mul(a, na_bits, b, nb_bits, out):
+    _check(load().gf2x_mul(_ptr(a), na_bits, _ptr(b), nb_bits, _ptr(out)), "gf2x_mul")
+
+
+def gf2x_mul_async(a, na_bits, b, nb_bits, out, stream=None):
+    _check(load().gf2x_mul_async(_ptr(a), na_bits, _ptr(b), nb_bits, _ptr(out), _stream(stream)),
+           "gf2x_mul_async")
+
+
+def gf2x_mul_host(a_host, na_bits, b_host, nb_bits, out_host, stream=None):
+    _check(load().gf2x_mul_host(_ptr(a_host), na_bits, _ptr(b_host), nb_bits, _ptr(out_host),
+                                _stream(stream)), "gf2x_mul_host")
+
+
+def gf2x_plan_create(na_bits, nb_bits):
+    p = _vp()
+    _check(load().gf2x_plan_create(na_bits, nb_bits, ctypes.byref(p)), "gf2x_plan_create")
+    return p.value
+
+
+def gf2x_plan_workspace_bytes(plan):
+    n = ctypes.c_size_t()
+    _check(load().gf2x_plan_workspace_bytes(plan, ctypes.byref(n)), "gf2x_plan_workspace_bytes")
+    return int(n.value)
+
+
+def gf2x_plan_execute(plan, a, b, out, workspace=None, stream=None):
+    _check(load().gf2x_plan_execute(plan, _ptr(a), _ptr(b), _ptr(out), _ptr(workspace),
+                                    _stream(stream)), "gf2x_plan_execute")
+
+
+def gf2x_plan_destroy(plan):
+    _check(load().gf2x_plan_destroy(plan), "gf2x_plan_destroy")
+
+
+def gf2x_mul_batched(a_list, na_bits, b_list, nb_bits, out_list, stream=None):
+    n = len(a_list)
+    P = ctypes.c_void_p * n
+    U = ctypes.c_uint64 * n
+    pa, pb, po = P(*[_ptr(x) for x in a_list]), P(*[_ptr(x) for x in b_list]), \
+        P(*[_ptr(x) for x in out_list])
+    na, nb = U(*[int(x) for x in na_bits]), U(*[int(x) for x in nb_bits])
+    _check(load().gf2x_mul_batched(n, ctypes.cast(pa, _vp), ctypes.cast(na, _vp),
+                                   ctypes.cast(pb, _vp), ctypes.cast(nb, _vp),
+                                   ctypes.cast(po, _vp), _stream(stream)), "gf2x_mul_batched")
+
+
+def gf2x_stage_basis_cvt64(f, log_n, inverse=0, stream=None):
+    _check(load().gf2x_stage_basis_cvt64(_ptr(f), log_n, inverse, _stream(stream)),
+           "gf2x_stage_basis_cvt64")
+
+
+def gf2x_stage_basis_cvt128(f, log_n, inverse=0, stream=None):
+    _check(load().gf2x_stage_basis_cvt128(_ptr(f), log_n, inverse, _stream(stream)),
+           "gf2x_stage_basis_cvt128")
+
+
+def gf2x_stage_chrepr(g, p, F, n, stream=None):
+    _check(load().gf2x_stage_chrepr(_ptr(g), p, _ptr(F), n, _stream(stream)), "gf2x_stage_chrepr")
+
+
+def gf2x_stage_fft(F, log_n, log_p, inverse=0, stream=None):
+    _check(load().gf2x_stage_fft(_ptr(F), log_n, log_p, inverse, _stream(stream)),
+           "gf2x_stage_fft")
+
+
+def gf2x_stage_pointmul(A, B, C, n, stream=None):
+    _check(load().gf2x_stage_pointmul(_ptr(A), _ptr(B), _ptr(C), n, _stream(stream)),
+           "gf2x_stage_pointmul")
+
+
+def gf2x_stage_ichrepr_combine(F, n, out, total_bits, stream=None):
+    _check(load().gf2x_stage_ichrepr_combine(_ptr(F), n, _ptr(out), total_bits, _stream(stream)),
+           "gf2x_stage_ichrepr_combine")
+
+
+def gf2x_shutdown():
+    _check(load().gf2x_shutdown(), "gf2x_shutdown")
+
+
+def gf2x_profile_enable(on=1):
+    _check(load().gf2x_profile_enable(int(on)), "gf2x_profile_enable")
+
+
+def gf2x_profile_reset():
+    _check(load().gf2x_profile_reset(), "gf2x_profile_reset")
+
+
+def gf2x_profile_read(stage):
+    """(ms, launches, calls) summed for stage index `stage`."""
+    ms = ctypes.c_double()
+    la = ctypes.c_uint64()
+    ca = ctypes.c_uint64()
+    _check(load().gf2x_profile_read(int(stage), ctypes.byref(ms), ctypes.byref(la),
+                                    ctypes.byref(ca)), "gf2x_profile_read")
+    return float(ms.value), int(la.value), int(ca.value)
+
+
+def gf2x_profile_stage_name(stage):
+    return load().gf2x_profile_stage_name(int(stage)).decode()
+
+
+def profile_all():
+    """{stage name: (ms, launches, calls)} for every stage."""
+    out = {}
+    i = 0
+    while True:
+        name = gf2x_profile_stage_name(i)
+        if not name:
+            return out
+        out[name] = gf2x_profile_read(i)
+        i += 1

@@ -1,0 +1,674 @@
+// The C ABI (include/gf2x_gb300.h): argument checks, per-device tables,
+// plans and the order of the stages of Alg. 5.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/gf2x_gb300.h"
+#include "gf2x_dev.cuh"
+#include "gf2x_internal.h"
+#include "kernels.h"
+
+using namespace gf2x;
+
+namespace {
+
+constexpr int kMaxLogN = 28;  // FFT points N <= 2^28
+
+// ---- Per-device context: the size-independent tables, uploaded once. ------
+struct DeviceCtx {
+    DevTables *tables = nullptr;
+};
+
+std::mutex g_ctx_mu;
+std::map<int, DeviceCtx> g_ctx;
+
+int current_device(int *dev) {
+    cudaError_t e = cudaGetDevice(dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return GF2X_ECUDA;
+    }
+    return GF2X_OK;
+}
+
+int get_tables(const DevTables **out) {
+    int dev;
+    int rc = current_device(&dev);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    DeviceCtx &c = g_ctx[dev];
+    if (!c.tables) {
+        const HostTables &H = host_tables();
+        std::unique_ptr<DevTables> h(new (std::nothrow) DevTables);
+        if (!h) return GF2X_ENOMEM;
+        static_assert(sizeof(h->S) == sizeof(H.S), "S layout");
+        std::memcpy(h->S, H.S, sizeof(H.S));
+        for (int p = 0; p < 8; p++)
+            for (int v = 0; v < 256; v++) {
+                const u128 &x = H.chr_in[p][v];
+                h->chr_in[p][v] = make_uint4((uint32_t)x.lo, (uint32_t)(x.lo >> 32),
+                                             (uint32_t)x.hi, (uint32_t)(x.hi >> 32));
+            }
+        for (int p = 0; p < 16; p++)
+            for (int v = 0; v < 256; v++) {
+                const u128 &x = H.chr_out[p][v];
+                h->chr_out[p][v] = make_uint4((uint32_t)x.lo, (uint32_t)(x.lo >> 32),
+                                              (uint32_t)x.hi, (uint32_t)(x.hi >> 32));
+            }
+        std::memcpy(h->gf8.log8, H.log8, sizeof(H.log8));
+        std::memcpy(h->gf8.exp8, H.exp8, sizeof(H.exp8));
+        std::memcpy(h->gf8.mul80, H.mul80, sizeof(H.mul80));
+        DevTables *d = nullptr;
+        if (cudaMalloc(&d, sizeof(DevTables)) != cudaSuccess) {
+            cudaGetLastError();
+            return GF2X_ENOMEM;
+        }
+        if (cudaMemcpy(d, h.get(), sizeof(DevTables), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(d);
+            return GF2X_ECUDA;
+        }
+        c.tables = d;
+    }
+    *out = c.tables;
+    return GF2X_OK;
+}
+
+int check_launch() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GF2X_OK : GF2X_ECUDA;
+}
+
+// Device (or managed) memory?  A null pointer is accepted only for size 0.
+int check_dev_ptr(const void *p, size_t bytes) {
+    if (bytes == 0) return GF2X_OK;
+    if (!p) return GF2X_EINVAL;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return GF2X_EINVAL;
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return GF2X_EINVAL;
+    return GF2X_OK;
+}
+
+bool overlap(const void *a, size_t na, const void *b, size_t nb) {
+    if (!na || !nb) return false;
+    auto x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
+uint64_t words_of(uint64_t bits) { return (bits + 63) / 64; }
+
+int log2_ceil(uint64_t n) {
+    int l = 0;
+    while ((1ull << l) < n) l++;
+    return l;
+}
+
+// ---- Per-stage timing (the component profile of Table 4) -------------------
+// When enabled, plan_run records a CUDA event before and after each stage on
+// the stream it runs on; gf2x_profile_read waits for the events and sums the
+// elapsed times per stage.
+enum Stage { ST_SPLIT, ST_BCVT, ST_CHREPR, ST_FFT, ST_POINTMUL, ST_IFFT, ST_IBCVT, ST_OUT, ST_COUNT };
+const char *kStageNames[ST_COUNT] = {"split",   "basis_cvt", "chrepr", "fft",
+                                     "pointmul", "ifft",      "ibasis_cvt", "ichrepr_combine"};
+
+struct ProfRec {
+    int stage;
+    cudaEvent_t a, b;
+    uint64_t launches;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_pending;
+double g_prof_ms[ST_COUNT];
+uint64_t g_prof_launches[ST_COUNT];
+uint64_t g_prof_calls[ST_COUNT];
+
+struct StageTimer {
+    cudaStream_t s;
+    bool on;
+    int stage = -1;
+    cudaEvent_t a = nullptr;
+    explicit StageTimer(cudaStream_t s_) : s(s_) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        on = g_prof_on;
+    }
+    void begin(int st) {
+        if (!on) return;
+        stage = st;
+        cudaEventCreate(&a);
+        cudaEventRecord(a, s);
+    }
+    void end(uint64_t launches) {
+        if (!on || stage < 0) return;
+        cudaEvent_t b;
+        cudaEventCreate(&b);
+        cudaEventRecord(b, s);
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_prof_pending.push_back(ProfRec{stage, a, b, launches});
+        stage = -1;
+    }
+};
+
+}  // namespace
+
+// ---- Plans ------------------------------------------------------------------
+struct gf2x_plan {
+    uint64_t na_bits, nb_bits, na_w, nb_w, out_words, total_bits;
+    int M, pa_log, pb_log;
+    uint64_t N, Pa, Pb;
+    std::vector<Level> lv_a, lv_b, lv_c;
+    // workspace layout (bytes): FA | FB | WA | WB
+    size_t off_fa, off_fb, off_wa, off_wb, ws_bytes;
+    int device;
+    std::mutex mu;
+    void *owned_ws = nullptr;
+};
+
+namespace {
+
+int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits) {
+    p->na_bits = na_bits;
+    p->nb_bits = nb_bits;
+    p->na_w = words_of(na_bits);
+    p->nb_w = words_of(nb_bits);
+    p->total_bits = na_bits + nb_bits - 1;
+    p->out_words = words_of(p->total_bits);
+    uint64_t need = std::max<uint64_t>(2, p->na_w + p->nb_w - 1);
+    p->M = log2_ceil(need);
+    if (p->M > kMaxLogN) return GF2X_EINVAL;
+    p->N = 1ull << p->M;
+    p->pa_log = log2_ceil(p->na_w);
+    p->pb_log = log2_ceil(p->nb_w);
+    p->Pa = 1ull << p->pa_log;
+    p->Pb = 1ull << p->pb_log;
+    p->lv_a = basis_cvt_levels(p->pa_log);
+    p->lv_b = basis_cvt_levels(p->pb_log);
+    p->lv_c = basis_cvt_levels(p->M);
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    p->off_fa = 0;
+    p->off_fb = up(p->off_fa + 16 * p->N);
+    p->off_wa = up(p->off_fb + 16 * p->N);
+    p->off_wb = up(p->off_wa + 8 * p->Pa);
+    p->ws_bytes = up(p->off_wb + 8 * p->Pb);
+    return current_device(&p->device);
+}
+
+// Alg. 5, stage after stage, on `s`.
+int plan_run(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out, void *ws,
+             cudaStream_t s) {
+    const DevTables *T;
+    int rc = get_tables(&T);
+    if (rc) return rc;
+    char *base = static_cast<char *>(ws);
+    uint4 *FA = reinterpret_cast<uint4 *>(base + p->off_fa);
+    uint4 *FB = reinterpret_cast<uint4 *>(base + p->off_fb);
+    uint64_t *WA = reinterpret_cast<uint64_t *>(base + p->off_wa);
+    uint64_t *WB = reinterpret_cast<uint64_t *>(base + p->off_wb);
+    auto mask_of = [](uint64_t bits) {
+        return (bits % 64) ? ((1ull << (bits % 64)) - 1) : ~0ull;
+    };
+    StageTimer tm(s);
+    uint64_t n;
+    // Split
+    tm.begin(ST_SPLIT);
+    launch_split_pad(a, p->na_w, mask_of(p->na_bits), WA, p->Pa, s);
+    launch_split_pad(b, p->nb_w, mask_of(p->nb_bits), WB, p->Pb, s);
+    tm.end(2);
+    // BasisCvt on the 64-bit blocks
+    tm.begin(ST_BCVT);
+    n = run_basis_cvt<uint64_t>(WA, p->pa_log, p->lv_a, 0, s);
+    n += run_basis_cvt<uint64_t>(WB, p->pb_log, p->lv_b, 0, s);
+    tm.end(n);
+    // changeRepr (+ fan-out of the layers above log2 P)
+    tm.begin(ST_CHREPR);
+    launch_chrepr(WA, p->Pa, FA, p->N, T, s);
+    launch_chrepr(WB, p->Pb, FB, p->N, T, s);
+    tm.end(2);
+    // FFT_LCH
+    tm.begin(ST_FFT);
+    n = run_fft(FA, p->M, p->pa_log, 0, T, s);
+    n += run_fft(FB, p->M, p->pb_log, 0, T, s);
+    tm.end(n);
+    // pointmul
+    tm.begin(ST_POINTMUL);
+    launch_pointmul(FA, FB, FB, p->N, T, s);
+    tm.end(1);
+    // iFFT_LCH, iBasisCvt
+    tm.begin(ST_IFFT);
+    n = run_fft(FB, p->M, p->M, 1, T, s);
+    tm.end(n);
+    tm.begin(ST_IBCVT);
+    n = run_basis_cvt<uint4>(FB, p->M, p->lv_c, 1, s);
+    tm.end(n);
+    // changeRepr^-1 + InterleavedCombine
+    tm.begin(ST_OUT);
+    launch_ichrepr_combine(FB, p->N, out, p->out_words, mask_of(p->total_bits), T, s);
+    tm.end(1);
+    return check_launch();
+}
+
+// Plan cache for the one-shot calls, keyed by (device, sizes).
+std::mutex g_cache_mu;
+std::map<std::tuple<int, uint64_t, uint64_t>, std::shared_ptr<gf2x_plan>> g_cache;
+
+int cached_plan(uint64_t na_bits, uint64_t nb_bits, std::shared_ptr<gf2x_plan> *out) {
+    int dev;
+    int rc = current_device(&dev);
+    if (rc) return rc;
+    auto key = std::make_tuple(dev, na_bits, nb_bits);
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+        *out = it->second;
+        return GF2X_OK;
+    }
+    auto p = std::make_shared<gf2x_plan>();
+    rc = plan_init(p.get(), na_bits, nb_bits);
+    if (rc) return rc;
+    if (g_cache.size() >= 256) g_cache.clear();
+    g_cache[key] = p;
+    *out = p;
+    return GF2X_OK;
+}
+
+int check_sizes(uint64_t na_bits, uint64_t nb_bits) {
+    if (na_bits > (1ull << 33) || nb_bits > (1ull << 33)) return GF2X_EINVAL;
+    return GF2X_OK;
+}
+
+int check_operands(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64_t nb_bits,
+                   const uint64_t *out) {
+    int rc = check_sizes(na_bits, nb_bits);
+    if (rc) return rc;
+    size_t ba = 8 * words_of(na_bits), bb = 8 * words_of(nb_bits);
+    size_t bo = 8 * gf2x_out_words(na_bits, nb_bits);
+    if ((rc = check_dev_ptr(a, ba))) return rc;
+    if ((rc = check_dev_ptr(b, bb))) return rc;
+    if ((rc = check_dev_ptr(out, bo))) return rc;
+    if (overlap(out, bo, a, ba) || overlap(out, bo, b, bb)) return GF2X_EINVAL;
+    return GF2X_OK;
+}
+
+int mul_on_stream(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64_t nb_bits,
+                  uint64_t *out, cudaStream_t s) {
+    std::shared_ptr<gf2x_plan> p;
+    int rc = cached_plan(na_bits, nb_bits, &p);
+    if (rc) return rc;
+    void *ws = nullptr;
+    if (cudaMallocAsync(&ws, p->ws_bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return GF2X_ENOMEM;
+    }
+    rc = plan_run(p.get(), a, b, out, ws, s);
+    cudaFreeAsync(ws, s);
+    if (rc == GF2X_OK) rc = check_launch();
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gf2x_strerror(int status) {
+    switch (status) {
+        case GF2X_OK: return "ok";
+        case GF2X_EINVAL: return "invalid argument";
+        case GF2X_ENOMEM: return "out of memory";
+        case GF2X_ECUDA: return "CUDA error (or no usable GPU)";
+        case GF2X_ETIMEOUT: return "timed out";
+        case GF2X_EBUSY: return "busy";
+        default: return "unknown status";
+    }
+}
+
+uint64_t gf2x_out_words(uint64_t na_bits, uint64_t nb_bits) {
+    if (!na_bits || !nb_bits) return 0;
+    return words_of(na_bits + nb_bits - 1);
+}
+
+uint64_t gf2x_fft_points(uint64_t na_bits, uint64_t nb_bits) {
+    if (!na_bits || !nb_bits) return 0;
+    uint64_t need = std::max<uint64_t>(2, words_of(na_bits) + words_of(nb_bits) - 1);
+    return 1ull << log2_ceil(need);
+}
+
+int gf2x_mul_async(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64_t nb_bits,
+                   uint64_t *out, gf2x_stream_t stream) {
+    try {
+        int rc = check_operands(a, na_bits, b, nb_bits, out);
+        if (rc) return rc;
+        if (!na_bits || !nb_bits) return GF2X_OK;
+        return mul_on_stream(a, na_bits, b, nb_bits, out, reinterpret_cast<cudaStream_t>(stream));
+    } catch (const std::bad_alloc &) {
+        return GF2X_ENOMEM;
+    } catch (...) {
+        return GF2X_ECUDA;
+    }
+}
+
+int gf2x_mul(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64_t nb_bits,
+             uint64_t *out) {
+    int rc = gf2x_mul_async(a, na_bits, b, nb_bits, out, nullptr);
+    if (rc) return rc;
+    if (cudaStreamSynchronize(0) != cudaSuccess) {
+        cudaGetLastError();
+        return GF2X_ECUDA;
+    }
+    return GF2X_OK;
+}
+
+int gf2x_mul_host(const uint64_t *a_host, uint64_t na_bits, const uint64_t *b_host,
+                  uint64_t nb_bits, uint64_t *out_host, gf2x_stream_t stream) {
+    try {
+        int rc = check_sizes(na_bits, nb_bits);
+        if (rc) return rc;
+        if (!na_bits || !nb_bits) return GF2X_OK;
+        if (!a_host || !b_host || !out_host) return GF2X_EINVAL;
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        size_t ba = 8 * words_of(na_bits), bb = 8 * words_of(nb_bits);
+        size_t bo = 8 * gf2x_out_words(na_bits, nb_bits);
+        std::shared_ptr<gf2x_plan> p;
+        if ((rc = cached_plan(na_bits, nb_bits, &p))) return rc;
+        char *buf = nullptr;
+        size_t total = p->ws_bytes + ((ba + 255) & ~255ull) + ((bb + 255) & ~255ull) + bo;
+        if (cudaMallocAsync(reinterpret_cast<void **>(&buf), total, s) != cudaSuccess) {
+            cudaGetLastError();
+            return GF2X_ENOMEM;
+        }
+        uint64_t *da = reinterpret_cast<uint64_t *>(buf + p->ws_bytes);
+        uint64_t *db = reinterpret_cast<uint64_t *>(buf + p->ws_bytes + ((ba + 255) & ~255ull));
+        uint64_t *dout = reinterpret_cast<uint64_t *>(buf + p->ws_bytes + ((ba + 255) & ~255ull) +
+                                                      ((bb + 255) & ~255ull));
+        cudaMemcpyAsync(da, a_host, ba, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(db, b_host, bb, cudaMemcpyHostToDevice, s);
+        rc = plan_run(p.get(), da, db, dout, buf, s);
+        cudaMemcpyAsync(out_host, dout, bo, cudaMemcpyDeviceToHost, s);
+        cudaFreeAsync(buf, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return GF2X_ECUDA;
+        }
+        return rc;
+    } catch (const std::bad_alloc &) {
+        return GF2X_ENOMEM;
+    } catch (...) {
+        return GF2X_ECUDA;
+    }
+}
+
+int gf2x_plan_create(uint64_t na_bits, uint64_t nb_bits, gf2x_plan **out) {
+    if (!out) return GF2X_EINVAL;
+    *out = nullptr;
+    try {
+        int rc = check_sizes(na_bits, nb_bits);
+        if (rc) return rc;
+        if (!na_bits || !nb_bits) return GF2X_EINVAL;
+        const DevTables *T;
+        if ((rc = get_tables(&T))) return rc;
+        gf2x_plan *p = new (std::nothrow) gf2x_plan();
+        if (!p) return GF2X_ENOMEM;
+        rc = plan_init(p, na_bits, nb_bits);
+        if (rc) {
+            delete p;
+            return rc;
+        }
+        *out = p;
+        return GF2X_OK;
+    } catch (const std::bad_alloc &) {
+        return GF2X_ENOMEM;
+    } catch (...) {
+        return GF2X_ECUDA;
+    }
+}
+
+int gf2x_plan_workspace_bytes(const gf2x_plan *p, size_t *bytes) {
+    if (!p || !bytes) return GF2X_EINVAL;
+    *bytes = p->ws_bytes;
+    return GF2X_OK;
+}
+
+int gf2x_plan_execute(gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out,
+                      void *workspace, gf2x_stream_t stream) {
+    if (!p) return GF2X_EINVAL;
+    try {
+        int rc = check_operands(a, p->na_bits, b, p->nb_bits, out);
+        if (rc) return rc;
+        int dev;
+        if ((rc = current_device(&dev))) return rc;
+        if (dev != p->device) return GF2X_EINVAL;
+        void *ws = workspace;
+        if (ws) {
+            if (reinterpret_cast<uintptr_t>(ws) & 255) return GF2X_EINVAL;
+            if ((rc = check_dev_ptr(ws, p->ws_bytes))) return rc;
+        } else {
+            std::lock_guard<std::mutex> lk(p->mu);
+            if (!p->owned_ws) {
+                if (cudaMalloc(&p->owned_ws, p->ws_bytes) != cudaSuccess) {
+                    cudaGetLastError();
+                    p->owned_ws = nullptr;
+                    return GF2X_ENOMEM;
+                }
+            }
+            ws = p->owned_ws;
+        }
+        return plan_run(p, a, b, out, ws, reinterpret_cast<cudaStream_t>(stream));
+    } catch (...) {
+        return GF2X_ECUDA;
+    }
+}
+
+int gf2x_plan_destroy(gf2x_plan *p) {
+    if (!p) return GF2X_EINVAL;
+    if (p->owned_ws) {
+        cudaDeviceSynchronize();
+        cudaFree(p->owned_ws);
+    }
+    delete p;
+    return GF2X_OK;
+}
+
+int gf2x_mul_batched(int count, const uint64_t *const *a, const uint64_t *na_bits,
+                     const uint64_t *const *b, const uint64_t *nb_bits, uint64_t *const *out,
+                     gf2x_stream_t stream) {
+    if (count < 0) return GF2X_EINVAL;
+    if (count == 0) return GF2X_OK;
+    if (!a || !na_bits || !b || !nb_bits || !out) return GF2X_EINVAL;
+    try {
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        std::vector<std::shared_ptr<gf2x_plan>> plans(count);
+        size_t ws_max = 0;
+        int rc;
+        for (int i = 0; i < count; i++) {
+            if ((rc = check_operands(a[i], na_bits[i], b[i], nb_bits[i], out[i]))) return rc;
+            if (!na_bits[i] || !nb_bits[i]) continue;
+            if ((rc = cached_plan(na_bits[i], nb_bits[i], &plans[i]))) return rc;
+            ws_max = std::max(ws_max, plans[i]->ws_bytes);
+        }
+        if (!ws_max) return GF2X_OK;
+        void *ws = nullptr;
+        if (cudaMallocAsync(&ws, ws_max, s) != cudaSuccess) {
+            cudaGetLastError();
+            return GF2X_ENOMEM;
+        }
+        rc = GF2X_OK;
+        for (int i = 0; i < count && rc == GF2X_OK; i++)
+            if (plans[i]) rc = plan_run(plans[i].get(), a[i], b[i], out[i], ws, s);
+        cudaFreeAsync(ws, s);
+        return rc;
+    } catch (const std::bad_alloc &) {
+        return GF2X_ENOMEM;
+    } catch (...) {
+        return GF2X_ECUDA;
+    }
+}
+
+// ---- Stage entry points -------------------------------------------------------
+
+int gf2x_stage_basis_cvt64(uint64_t *f, int log_n, int inverse, gf2x_stream_t stream) {
+    if (log_n < 0 || log_n > kMaxLogN + 1) return GF2X_EINVAL;
+    int rc = check_dev_ptr(f, 8ull << log_n);
+    if (rc) return rc;
+    try {
+        run_basis_cvt<uint64_t>(f, log_n, basis_cvt_levels(log_n), inverse ? 1 : 0,
+                                reinterpret_cast<cudaStream_t>(stream));
+    } catch (...) {
+        return GF2X_ECUDA;
+    }
+    return check_launch();
+}
+
+int gf2x_stage_basis_cvt128(uint64_t *f, int log_n, int inverse, gf2x_stream_t stream) {
+    if (log_n < 0 || log_n > kMaxLogN) return GF2X_EINVAL;
+    int rc = check_dev_ptr(f, 16ull << log_n);
+    if (rc) return rc;
+    if (reinterpret_cast<uintptr_t>(f) & 15) return GF2X_EINVAL;
+    try {
+        run_basis_cvt<uint4>(reinterpret_cast<uint4 *>(f), log_n, basis_cvt_levels(log_n),
+                             inverse ? 1 : 0, reinterpret_cast<cudaStream_t>(stream));
+    } catch (...) {
+        return GF2X_ECUDA;
+    }
+    return check_launch();
+}
+
+int gf2x_stage_chrepr(const uint64_t *g, uint64_t p, uint64_t *F, uint64_t n,
+                      gf2x_stream_t stream) {
+    if (p == 0 || (p & (p - 1)) || n == 0 || (n & (n - 1)) || p > n || n > (1ull << kMaxLogN))
+        return GF2X_EINVAL;
+    int rc;
+    if ((rc = check_dev_ptr(g, 8 * p)) || (rc = check_dev_ptr(F, 16 * n))) return rc;
+    if (reinterpret_cast<uintptr_t>(F) & 15) return GF2X_EINVAL;
+    const DevTables *T;
+    if ((rc = get_tables(&T))) return rc;
+    launch_chrepr(g, p, reinterpret_cast<uint4 *>(F), n, T, reinterpret_cast<cudaStream_t>(stream));
+    return check_launch();
+}
+
+int gf2x_stage_fft(uint64_t *F, int log_n, int log_p, int inverse, gf2x_stream_t stream) {
+    if (log_n < 0 || log_n > kMaxLogN || log_p < 0 || log_p > log_n) return GF2X_EINVAL;
+    int rc = check_dev_ptr(F, 16ull << log_n);
+    if (rc) return rc;
+    if (reinterpret_cast<uintptr_t>(F) & 15) return GF2X_EINVAL;
+    const DevTables *T;
+    if ((rc = get_tables(&T))) return rc;
+    run_fft(reinterpret_cast<uint4 *>(F), log_n, inverse ? log_n : log_p, inverse ? 1 : 0, T,
+            reinterpret_cast<cudaStream_t>(stream));
+    return check_launch();
+}
+
+int gf2x_stage_pointmul(const uint64_t *A, const uint64_t *B, uint64_t *C, uint64_t n,
+                        gf2x_stream_t stream) {
+    if (n > (1ull << kMaxLogN)) return GF2X_EINVAL;
+    int rc;
+    if ((rc = check_dev_ptr(A, 16 * n)) || (rc = check_dev_ptr(B, 16 * n)) ||
+        (rc = check_dev_ptr(C, 16 * n)))
+        return rc;
+    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) |
+         reinterpret_cast<uintptr_t>(C)) & 15)
+        return GF2X_EINVAL;
+    if (n == 0) return GF2X_OK;
+    const DevTables *T;
+    if ((rc = get_tables(&T))) return rc;
+    launch_pointmul(reinterpret_cast<const uint4 *>(A), reinterpret_cast<const uint4 *>(B),
+                    reinterpret_cast<uint4 *>(C), n, T, reinterpret_cast<cudaStream_t>(stream));
+    return check_launch();
+}
+
+int gf2x_stage_ichrepr_combine(const uint64_t *F, uint64_t n, uint64_t *out, uint64_t total_bits,
+                               gf2x_stream_t stream) {
+    if (n > (1ull << kMaxLogN)) return GF2X_EINVAL;
+    uint64_t ow = words_of(total_bits);
+    int rc;
+    if ((rc = check_dev_ptr(F, 16 * n)) || (rc = check_dev_ptr(out, 8 * ow))) return rc;
+    if (reinterpret_cast<uintptr_t>(F) & 15) return GF2X_EINVAL;
+    if (overlap(out, 8 * ow, F, 16 * n)) return GF2X_EINVAL;
+    if (ow == 0) return GF2X_OK;
+    const DevTables *T;
+    if ((rc = get_tables(&T))) return rc;
+    uint64_t mask = (total_bits % 64) ? ((1ull << (total_bits % 64)) - 1) : ~0ull;
+    launch_ichrepr_combine(reinterpret_cast<const uint4 *>(F), n, out, ow, mask, T,
+                           reinterpret_cast<cudaStream_t>(stream));
+    return check_launch();
+}
+
+int gf2x_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return GF2X_OK;
+}
+
+int gf2x_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &r : g_prof_pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_prof_pending.clear();
+    for (int i = 0; i < ST_COUNT; i++) {
+        g_prof_ms[i] = 0;
+        g_prof_launches[i] = 0;
+        g_prof_calls[i] = 0;
+    }
+    cudaGetLastError();
+    return GF2X_OK;
+}
+
+int gf2x_profile_read(int stage, double *ms, uint64_t *launches, uint64_t *calls) {
+    if (stage < 0 || stage >= ST_COUNT || !ms || !launches || !calls) return GF2X_EINVAL;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int rc = GF2X_OK;
+    for (auto &r : g_prof_pending) {
+        float t = 0;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess)
+            rc = GF2X_ECUDA;
+        g_prof_ms[r.stage] += t;
+        g_prof_launches[r.stage] += r.launches;
+        g_prof_calls[r.stage] += 1;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_prof_pending.clear();
+    cudaGetLastError();
+    *ms = g_prof_ms[stage];
+    *launches = g_prof_launches[stage];
+    *calls = g_prof_calls[stage];
+    return rc;
+}
+
+const char *gf2x_profile_stage_name(int stage) {
+    if (stage < 0 || stage >= ST_COUNT) return "";
+    return kStageNames[stage];
+}
+
+int gf2x_shutdown(void) {
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        g_cache.clear();
+    }
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    int cur = -1;
+    cudaGetDevice(&cur);
+    for (auto &kv : g_ctx) {
+        if (kv.second.tables) {
+            cudaSetDevice(kv.first);
+            cudaDeviceSynchronize();
+            cudaFree(kv.second.tables);
+            kv.second.tables = nullptr;
+        }
+    }
+    if (cur >= 0) cudaSetDevice(cur);
+    cudaGetLastError();
+    return GF2X_OK;
+}
+
+}  // extern "C"

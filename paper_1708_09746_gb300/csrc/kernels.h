@@ -1,0 +1,42 @@
+// Host launchers of the CUDA kernels (kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "gf2x_internal.h"
+
+namespace gf2x {
+
+struct DevTables;
+
+// Consecutive BasisCvt levels applied inside one shared-memory tile.
+struct LevelBatch {
+    static constexpr int kMax = 48;
+    int count;
+    int8_t logE[kMax];
+    int8_t loge[kMax];
+};
+
+void launch_split_pad(const uint64_t *a, uint64_t nw, uint64_t last_mask, uint64_t *w, uint64_t P,
+                      cudaStream_t s);
+
+// BasisCvt (inverse = 0) or iBasisCvt (inverse = 1) on 2^m coefficients of
+// type T (uint64_t or uint4), with the forward level list `fwd`.  The run_*
+// launchers return the number of kernel launches they enqueued.
+template <typename T>
+uint64_t run_basis_cvt(T *f, int m, const std::vector<Level> &fwd, int inverse, cudaStream_t s);
+
+void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const DevTables *T,
+                   cudaStream_t s);
+
+uint64_t run_fft(uint4 *F, int log_n, int log_p, int inverse, const DevTables *T, cudaStream_t s);
+
+void launch_pointmul(const uint4 *A, const uint4 *B, uint4 *C, uint64_t n, const DevTables *T,
+                     cudaStream_t s);
+
+void launch_ichrepr_combine(const uint4 *F, uint64_t n, uint64_t *out, uint64_t out_words,
+                            uint64_t last_mask, const DevTables *T, cudaStream_t s);
+
+}  // namespace gf2x

@@ -1,0 +1,132 @@
+"""Parity of the whole product path (gf2x_mul through the C ABI) with the
+CPU oracle, bit-exact, on seeded inputs."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1708_09746_gb300 as G
+from oracle import product as P
+import workloads as W
+
+from gpu_util import empty_dev, from_dev, gpu_mul, need_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def test_c0_2pow20_seed0():
+    # 2^20 x 2^20 bits, seed 0, top bits forced: a 2^21-1-bit product.
+    a, na, b, nb = W.make_workload("c0_2^20")
+    got = gpu_mul(a, na, b, nb)
+    want = P.mul(a, na, b, nb)
+    assert np.array_equal(got, want)
+
+
+SMALL = [(1, 1), (1, 64), (64, 1), (64, 64), (65, 63), (127, 129), (128, 128),
+         (200, 3000), (3000, 200), (4096, 4096), (4097, 1), (1, 4097), (640, 700),
+         (64 * 33, 64 * 31 + 5), (8191, 8193), (65536, 65536), (65536, 65535),
+         (100000, 3), (131072 + 64, 131072 - 64)]
+
+
+@pytest.mark.parametrize("na,nb", SMALL)
+def test_small_and_ragged(na, nb):
+    a, b = W.operand_pair(na * 31 + nb, na, nb)
+    got = gpu_mul(a, na, b, nb)
+    assert np.array_equal(got, P.mul(a, na, b, nb))
+
+
+def test_random_sizes_sweep():
+    rng = np.random.default_rng(77)
+    for it in range(40):
+        na = int(rng.integers(1, 1 << int(rng.integers(1, 17))))
+        nb = int(rng.integers(1, 1 << int(rng.integers(1, 17))))
+        a, b = W.operand_pair(1000 + it, na, nb, top_bit=bool(it % 2))
+        assert np.array_equal(gpu_mul(a, na, b, nb), P.mul(a, na, b, nb)), (na, nb)
+
+
+def test_bits_past_length_ignored():
+    na, nb = 1000, 777
+    a, b = W.operand_pair(5, na, nb)
+    a_dirty, b_dirty = a.copy(), b.copy()
+    a_dirty[-1] |= np.uint64(~((1 << (na % 64)) - 1) & (2**64 - 1))
+    b_dirty[-1] |= np.uint64(~((1 << (nb % 64)) - 1) & (2**64 - 1))
+    assert np.array_equal(gpu_mul(a_dirty, na, b_dirty, nb), P.mul(a, na, b, nb))
+
+
+def test_all_ones_and_sparse():
+    n = 1 << 18
+    o = W.all_ones(n)
+    assert np.array_equal(gpu_mul(o, n, o, n), P.mul(o, n, o, n))
+    s1 = W.sparse_poly(3, n)
+    s2 = W.sparse_poly(1003, n)
+    assert np.array_equal(gpu_mul(s1, n, s2, n), P.mul(s1, n, s2, n))
+
+
+def test_zero_length_operand_writes_nothing():
+    a = to_dev(W.uniform_poly(1, 100))
+    out = torch.full((4,), 7, dtype=torch.int64, device="cuda")
+    G.gf2x_mul(a, 100, a, 0, out)
+    torch.cuda.synchronize()
+    assert from_dev(out).tolist() == [7, 7, 7, 7]
+
+
+def test_invalid_arguments():
+    a = to_dev(W.uniform_poly(1, 640))
+    out = empty_dev(32)
+    # host pointer
+    host = np.zeros(32, dtype=np.uint64)
+    with pytest.raises(G.GF2XError) as e:
+        G.gf2x_mul(host, 640, a, 640, out)
+    assert e.value.status == -1
+    # overlapping output
+    with pytest.raises(G.GF2XError):
+        G.gf2x_mul(a, 640, a, 640, a)
+    # too large
+    with pytest.raises(G.GF2XError):
+        G.gf2x_mul(a, 1 << 40, a, 640, out)
+
+
+def test_plan_api_and_host_api():
+    na, nb = 50000, 70001
+    a, b = W.operand_pair(9, na, nb)
+    want = P.mul(a, na, b, nb)
+    plan = G.gf2x_plan_create(na, nb)
+    try:
+        ws_bytes = G.gf2x_plan_workspace_bytes(plan)
+        ws = torch.empty(ws_bytes // 8 + 32, dtype=torch.int64, device="cuda")
+        da, db = to_dev(a), to_dev(b)
+        out = empty_dev(len(want))
+        s = torch.cuda.Stream()
+        G.gf2x_plan_execute(plan, da, db, out, ws, s)
+        s.synchronize()
+        assert np.array_equal(from_dev(out, len(want)), want)
+        out2 = empty_dev(len(want))
+        G.gf2x_plan_execute(plan, da, db, out2, None, None)
+        torch.cuda.synchronize()
+        assert np.array_equal(from_dev(out2, len(want)), want)
+    finally:
+        G.gf2x_plan_destroy(plan)
+    host_out = np.zeros(len(want), dtype=np.uint64)
+    G.gf2x_mul_host(a, na, b, nb, host_out)
+    assert np.array_equal(host_out, want)
+
+
+def test_batched_uneven():
+    lens = W.log_uniform_lengths(7, 24, 6, 16)
+    pairs = []
+    for i in range(0, 24, 2):
+        na, nb = int(lens[i]), int(lens[i + 1])
+        a, b = W.operand_pair(500 + i, na, nb)
+        pairs.append((a, na, b, nb))
+    da = [to_dev(p[0]) for p in pairs]
+    db = [to_dev(p[2]) for p in pairs]
+    outs = [empty_dev(G.gf2x_out_words(p[1], p[3])) for p in pairs]
+    G.gf2x_mul_batched(da, [p[1] for p in pairs], db, [p[3] for p in pairs], outs)
+    torch.cuda.synchronize()
+    for p, o in zip(pairs, outs):
+        want = P.mul(p[0], p[1], p[2], p[3])
+        assert np.array_equal(from_dev(o, len(want)), want)

@@ -161,3 +161,14 @@ def test_fingerprint_detects_errors():
     bad = c.copy()
     bad[17] ^= np.uint64(1 << 5)
     assert not P.fingerprint_ok(a, na, b, nb, bad, r)
+
+
+def test_product_word_matches_full_product():
+    na, nb = 64 * 50 + 3, 64 * 31 + 60
+    a, b = W.operand_pair(31, na, nb)
+    full = P.mul_bits(a, na, b, nb)
+    for j in range(len(full)):
+        w = P.product_word(a, na, b, nb, j)
+        if j == len(full) - 1 and (na + nb - 1) % 64:
+            w &= (1 << ((na + nb - 1) % 64)) - 1
+        assert w == int(full[j])
