@@ -165,8 +165,10 @@ GF2X_API int gf2x_stage_ichrepr_combine(const uint64_t *F, uint64_t n, uint64_t 
 /* ---- Per-stage timing (the component profile of the paper's Table 4) ----*/
 
 /* on = 1: every later product records a CUDA event before and after each of
- * its stages (split, basis_cvt, chrepr, fft, pointmul, ifft, ibasis_cvt,
- * ichrepr_combine) on the stream it runs on.  on = 0 stops recording. */
+ * its stage groups on the stream it runs on: split, basis_cvt, chrepr_fft_a
+ * (changeRepr + FFT_LCH of a), chrepr_fft_b (changeRepr + top FFT_LCH layers
+ * of b), fft_pointmul_ifft_bottom (bottom FFT layers of b + pointmul + bottom
+ * iFFT layers), ifft_top, ibasis_cvt, ichrepr_combine.  on = 0 stops. */
 GF2X_API int gf2x_profile_enable(int on);
 
 /* Drops recorded events and zeroes the sums. */

@@ -12,6 +12,7 @@
 #include "../../include/gf2x_gb300.h"
 #include "gf2x_dev.cuh"
 #include "gf2x_internal.h"
+#include "fft_pass.h"
 #include "kernels.h"
 
 using namespace gf2x;
@@ -61,9 +62,8 @@ int get_tables(const DevTables **out) {
                 h->chr_out[p][v] = make_uint4((uint32_t)x.lo, (uint32_t)(x.lo >> 32),
                                               (uint32_t)x.hi, (uint32_t)(x.hi >> 32));
             }
-        std::memcpy(h->gf8.log8, H.log8, sizeof(H.log8));
-        std::memcpy(h->gf8.exp8, H.exp8, sizeof(H.exp8));
-        std::memcpy(h->gf8.mul80, H.mul80, sizeof(H.mul80));
+        std::memcpy(h->mul8, H.mul8, sizeof(H.mul8));
+        std::memcpy(h->shfl_basis, H.shfl_basis, sizeof(H.shfl_basis));
         DevTables *d = nullptr;
         if (cudaMalloc(&d, sizeof(DevTables)) != cudaSuccess) {
             cudaGetLastError();
@@ -117,9 +117,10 @@ int log2_ceil(uint64_t n) {
 // When enabled, plan_run records a CUDA event before and after each stage on
 // the stream it runs on; gf2x_profile_read waits for the events and sums the
 // elapsed times per stage.
-enum Stage { ST_SPLIT, ST_BCVT, ST_CHREPR, ST_FFT, ST_POINTMUL, ST_IFFT, ST_IBCVT, ST_OUT, ST_COUNT };
-const char *kStageNames[ST_COUNT] = {"split",   "basis_cvt", "chrepr", "fft",
-                                     "pointmul", "ifft",      "ibasis_cvt", "ichrepr_combine"};
+enum Stage { ST_SPLIT, ST_BCVT, ST_FFT_A, ST_FFT_B, ST_FUSED, ST_IFFT, ST_IBCVT, ST_OUT, ST_COUNT };
+const char *kStageNames[ST_COUNT] = {"split",        "basis_cvt",      "chrepr_fft_a",
+                                     "chrepr_fft_b", "fft_pointmul_ifft_bottom", "ifft_top",
+                                     "ibasis_cvt",   "ichrepr_combine"};
 
 struct ProfRec {
     int stage;
@@ -167,6 +168,10 @@ struct gf2x_plan {
     int M, pa_log, pb_log;
     uint64_t N, Pa, Pb;
     std::vector<Level> lv_a, lv_b, lv_c;
+    // FFT pass schedules: forward of a; forward of b whose bottom pass also
+    // does pointmul and the bottom inverse layers; the inverse top layers.
+    std::vector<FftPassCfg> fft_a, fft_b, ifft_top;
+    FftPassCfg fused;
     // workspace layout (bytes): FA | FB | WA | WB
     size_t off_fa, off_fb, off_wa, off_wb, ws_bytes;
     int device;
@@ -194,6 +199,9 @@ int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits) {
     p->lv_a = basis_cvt_levels(p->pa_log);
     p->lv_b = basis_cvt_levels(p->pb_log);
     p->lv_c = basis_cvt_levels(p->M);
+    int rc = plan_fft_forward(p->M, p->pa_log, p->fft_a);
+    if (rc) return rc;
+    if ((rc = plan_fft_fused(p->M, p->pb_log, p->fft_b, p->fused, p->ifft_top))) return rc;
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     p->off_fa = 0;
     p->off_fb = up(p->off_fa + 16 * p->N);
@@ -230,23 +238,24 @@ int plan_run(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t 
     n += run_basis_cvt<uint64_t>(WB, p->pb_log, p->lv_b, 0, s);
     tm.end(n);
     // changeRepr (+ fan-out of the layers above log2 P)
-    tm.begin(ST_CHREPR);
-    launch_chrepr(WA, p->Pa, FA, p->N, T, s);
-    launch_chrepr(WB, p->Pb, FB, p->N, T, s);
-    tm.end(2);
-    // FFT_LCH
-    tm.begin(ST_FFT);
-    n = run_fft(FA, p->M, p->pa_log, 0, T, s);
-    n += run_fft(FB, p->M, p->pb_log, 0, T, s);
-    tm.end(n);
-    // pointmul
-    tm.begin(ST_POINTMUL);
-    launch_pointmul(FA, FB, FB, p->N, T, s);
+    // changeRepr + FFT_LCH of a (changeRepr fused into the first pass)
+    tm.begin(ST_FFT_A);
+    for (size_t i = 0; i < p->fft_a.size(); i++)
+        launch_fft_pass(p->fft_a[i], p->M, FA, i == 0 ? WA : nullptr, p->Pa, nullptr, T, s);
+    tm.end(p->fft_a.size());
+    // changeRepr + FFT_LCH of b, top layers
+    tm.begin(ST_FFT_B);
+    for (size_t i = 0; i < p->fft_b.size(); i++)
+        launch_fft_pass(p->fft_b[i], p->M, FB, i == 0 ? WB : nullptr, p->Pb, nullptr, T, s);
+    tm.end(p->fft_b.size());
+    // bottom layers of FFT(b), pointmul, bottom layers of iFFT_LCH
+    tm.begin(ST_FUSED);
+    launch_fft_pass(p->fused, p->M, FB, p->fft_b.empty() ? WB : nullptr, p->Pb, FA, T, s);
     tm.end(1);
-    // iFFT_LCH, iBasisCvt
+    // iFFT_LCH top layers, iBasisCvt
     tm.begin(ST_IFFT);
-    n = run_fft(FB, p->M, p->M, 1, T, s);
-    tm.end(n);
+    for (auto &ps : p->ifft_top) launch_fft_pass(ps, p->M, FB, nullptr, 0, nullptr, T, s);
+    tm.end(p->ifft_top.size());
     tm.begin(ST_IBCVT);
     n = run_basis_cvt<uint4>(FB, p->M, p->lv_c, 1, s);
     tm.end(n);
@@ -561,8 +570,16 @@ int gf2x_stage_fft(uint64_t *F, int log_n, int log_p, int inverse, gf2x_stream_t
     if (reinterpret_cast<uintptr_t>(F) & 15) return GF2X_EINVAL;
     const DevTables *T;
     if ((rc = get_tables(&T))) return rc;
-    run_fft(reinterpret_cast<uint4 *>(F), log_n, inverse ? log_n : log_p, inverse ? 1 : 0, T,
-            reinterpret_cast<cudaStream_t>(stream));
+    try {
+        std::vector<FftPassCfg> passes;
+        rc = inverse ? plan_fft_inverse(log_n, passes) : plan_fft_forward(log_n, log_p, passes);
+        if (rc) return rc;
+        for (auto &ps : passes)
+            launch_fft_pass(ps, log_n, reinterpret_cast<uint4 *>(F), nullptr, 0, nullptr, T,
+                            reinterpret_cast<cudaStream_t>(stream));
+    } catch (...) {
+        return GF2X_ECUDA;
+    }
     return check_launch();
 }
 
@@ -579,8 +596,8 @@ int gf2x_stage_pointmul(const uint64_t *A, const uint64_t *B, uint64_t *C, uint6
     if (n == 0) return GF2X_OK;
     const DevTables *T;
     if ((rc = get_tables(&T))) return rc;
-    launch_pointmul(reinterpret_cast<const uint4 *>(A), reinterpret_cast<const uint4 *>(B),
-                    reinterpret_cast<uint4 *>(C), n, T, reinterpret_cast<cudaStream_t>(stream));
+    launch_pointmul_mt(reinterpret_cast<const uint4 *>(A), reinterpret_cast<const uint4 *>(B),
+                       reinterpret_cast<uint4 *>(C), n, T, reinterpret_cast<cudaStream_t>(stream));
     return check_launch();
 }
 

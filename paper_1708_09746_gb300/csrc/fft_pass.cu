@@ -1,0 +1,411 @@
+// Fused multi-layer passes of FFT_LCH (Alg. 1) and its inverse.
+//
+// A pass covers the g consecutive layers k_lo .. k_lo+g-1 of the N-point
+// transform.  Its CTA owns a tile of 2^g "rows" (index bits k_lo .. k_lo+g-1)
+// by 2^c "columns" (index bits 0 .. c-1, consecutive elements, so that the
+// tile moves through HBM in 512-byte runs); the remaining index bits name the
+// CTA.  The tile is loaded into shared memory once, all g layers are applied,
+// and it is written back once.
+//
+// Multiplier of a butterfly of layer k = k_lo + r at tile row `row`:
+//   s_k(phi(idx with bits <= k cleared))
+//     = s_k(phi(hi << (k_lo+g)))  XOR  s_k(phi((row >> (r+1)) << (k+1)))
+//     =        cval[r]            XOR       d(k, row >> (r+1))
+// by the linearity of s_k (Sec. 4.4).  cval[r] is the same for the whole CTA;
+// d(k, prefix) is the same for every tile and is precomputed per pass.
+//
+// Layers whose butterflies can be laid out so that the 32 lanes of a warp
+// share the multiplier (column bits plus lower rows span >= 5 index bits) are
+// processed four at a time in registers with warp-shuffle tables (the table
+// of cval[r] is built once per CTA, the table of d is precomputed; the table
+// of their sum is the XOR of the two).  The lowest layers of the contiguous
+// bottom pass (k < 5, multiplier changes every 2^(k+1) elements) use the
+// F~_{2^8} product table in shared memory, one layer per sweep.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "fft_pass.h"
+#include "gf2x_internal.h"
+#include "gf2x_mul.cuh"
+
+namespace gf2x {
+
+// ---------------------------------------------------------------------------
+// Register sub-pass: G layers (tile rows r_lo .. r_lo+G-1) on columns of 2^G
+// elements held by one thread.  Requires c + r_lo >= 5 so that a warp's lanes
+// differ only in bits below the sub-pass (warp-uniform multipliers).
+template <int G, bool INV>
+__device__ __forceinline__ void reg_subpass(uint4 *s, int c, int g, int r_lo, int uf,
+                                            const uint32_t *ctab, const uint32_t *__restrict__ d_shfl) {
+    const int r_hi = r_lo + G - 1;
+    const uint32_t items = 1u << (g + c - G);
+    const int lane = threadIdx.x & 31;
+    const uint32_t cmask = (1u << c) - 1, lomask = (1u << r_lo) - 1;
+    for (uint32_t q = threadIdx.x; q < items; q += blockDim.x) {
+        const uint32_t col = q & cmask, rest = q >> c;
+        const uint32_t lo_rows = rest & lomask, hi_rows = rest >> r_lo;
+        const uint32_t base_row = (hi_rows << (r_hi + 1)) | lo_rows;
+        uint4 e[1 << G];
+#pragma unroll
+        for (int m = 0; m < (1 << G); m++) e[m] = s[((base_row | ((uint32_t)m << r_lo)) << c) | col];
+#pragma unroll
+        for (int step = 0; step < G; step++) {
+            const int rr = INV ? step : (G - 1 - step);
+            const int r = r_lo + rr;
+            // offset (in multipliers) of layer r's precomputed tables
+            const uint32_t off = (1u << (g - uf)) - (1u << (g - r));
+#pragma unroll
+            for (int B = 0; B < (1 << (G - 1 - rr)); B++) {
+                const uint32_t prefix = (hi_rows << (r_hi - r)) | (uint32_t)B;
+                ShflTab T;
+                const uint32_t *dp = d_shfl + (size_t)(off + prefix) * 224 + lane;
+                const uint32_t *cp = ctab + (r - uf) * 224 + lane;
+#pragma unroll
+                for (int w = 0; w < 7; w++) T.t[w] = cp[32 * w] ^ __ldg(dp + 32 * w);
+#pragma unroll
+                for (int j = 0; j < (1 << rr); j++) {
+                    uint4 &u = e[B * (2 << rr) + j];
+                    uint4 &v = e[B * (2 << rr) + j + (1 << rr)];
+                    if (!INV) {
+                        u = xor4(u, shfl_mul128(v, T));
+                        v = xor4(v, u);
+                    } else {
+                        v = xor4(v, u);
+                        u = xor4(u, shfl_mul128(v, T));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < (1 << G); m++) s[((base_row | ((uint32_t)m << r_lo)) << c) | col] = e[m];
+    }
+}
+
+template <bool INV>
+__device__ __forceinline__ void run_subpass(int G, uint4 *s, int c, int g, int r_lo, int uf,
+                                            const uint32_t *ctab, const uint32_t *d_shfl) {
+    switch (G) {
+        case 1: reg_subpass<1, INV>(s, c, g, r_lo, uf, ctab, d_shfl); break;
+        case 2: reg_subpass<2, INV>(s, c, g, r_lo, uf, ctab, d_shfl); break;
+        case 3: reg_subpass<3, INV>(s, c, g, r_lo, uf, ctab, d_shfl); break;
+        default: reg_subpass<4, INV>(s, c, g, r_lo, uf, ctab, d_shfl); break;
+    }
+}
+
+// One lane-varying layer r of a contiguous tile (c = 0) swept in shared memory.
+template <bool INV>
+__device__ __forceinline__ void smem_layer(uint4 *s, int g, int r, const uint8_t *mt, uint32_t cv,
+                                           const uint32_t *__restrict__ d_val) {
+    const uint32_t half = 1u << (g - 1);
+    const uint32_t voff = (1u << g) - (1u << (g - r));
+    for (uint32_t w = threadIdx.x; w < half; w += blockDim.x) {
+        const uint32_t prefix = w >> r, j = w & ((1u << r) - 1);
+        const uint32_t iu = (prefix << (r + 1)) | j, iv = iu | (1u << r);
+        const MtConst mc = mt_prep(mt, cv ^ __ldg(d_val + voff + prefix));
+        uint4 u = s[iu], v = s[iv];
+        if (!INV) {
+            u = xor4(u, mt_cmul128(mt, v, mc));
+            v = xor4(v, u);
+        } else {
+            v = xor4(v, u);
+            u = xor4(u, mt_cmul128(mt, v, mc));
+        }
+        s[iu] = u;
+        s[iv] = v;
+    }
+}
+
+__device__ __forceinline__ uint4 chrepr_ldg(const DevTables *__restrict__ T, uint64_t w) {
+    uint4 acc = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int p = 0; p < 8; p++) acc = xor4(acc, __ldg(&T->chr_in[p][(w >> (8 * p)) & 255]));
+    return acc;
+}
+
+__global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int g = a.g, c = a.c, uf = a.uf;
+    const uint32_t tile = 1u << (g + c);
+    uint4 *s = reinterpret_cast<uint4 *>(smem);
+    uint32_t *ctab = reinterpret_cast<uint32_t *>(smem + 16 * (size_t)tile);  // [g-uf][7][32]
+    uint32_t *cval = ctab + (g - uf) * 224;                                   // [g]
+    uint8_t *mt = reinterpret_cast<uint8_t *>(cval + 32);                    // 64 KiB if needed
+
+    const int mid_bits = a.k_lo - c;
+    const uint32_t mid = blockIdx.x & ((1u << mid_bits) - 1);
+    const uint32_t hi = blockIdx.x >> mid_bits;
+    const uint32_t base = (hi << (a.k_lo + g)) | (mid << c);
+    const uint32_t cmask = (1u << c) - 1;
+
+    // multipliers shared by the whole CTA
+    if ((int)threadIdx.x < g) {
+        const int k = a.k_lo + threadIdx.x;
+        cval[threadIdx.x] = s_k_of(&a.T->S[k][0], hi << (a.k_lo + g));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (g - uf) * 224; i += blockDim.x) {
+        const int r = uf + i / 224, wl = i % 224;
+        uint32_t cv = cval[r], acc = 0;
+        const uint32_t *b = &a.T->shfl_basis[0][0][0] + wl;
+        while (cv) {
+            const int t = __ffs(cv) - 1;
+            acc ^= __ldg(b + t * 224);
+            cv &= cv - 1;
+        }
+        ctab[i] = acc;
+    }
+    if (a.needs_mt) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.T->mul8);
+        uint4 *dst = reinterpret_cast<uint4 *>(mt);
+        for (int i = threadIdx.x; i < 4096; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    // load the tile (changeRepr on the fly when reading the 64-bit blocks)
+    for (uint32_t i = threadIdx.x; i < tile; i += blockDim.x) {
+        const uint32_t row = i >> c, col = i & cmask;
+        const uint32_t idx = base | (row << a.k_lo) | col;
+        s[i] = a.g64 ? chrepr_ldg(a.T, __ldg(a.g64 + (idx & a.pmask))) : a.F[idx];
+    }
+    __syncthreads();
+
+    if (a.mode != 1) {  // forward layers g_f-1 .. 0
+        for (int r_hi = a.g_f - 1; r_hi >= uf; r_hi -= 4) {
+            const int r_lo = max(uf, r_hi - 3);
+            run_subpass<false>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab, a.d_shfl);
+            __syncthreads();
+        }
+        for (int r = min(uf, a.g_f) - 1; r >= 0; r--) {
+            smem_layer<false>(s, g, r, mt, cval[r], a.d_val);
+            __syncthreads();
+        }
+    }
+    if (a.mode == 2) {  // pointmul with the other operand's transform
+        for (uint32_t i = threadIdx.x; i < tile; i += blockDim.x) {
+            const uint32_t row = i >> c, col = i & cmask;
+            const uint32_t idx = base | (row << a.k_lo) | col;
+            s[i] = mt_gmul128(mt, s[i], __ldg(a.FA + idx));
+        }
+        __syncthreads();
+    }
+    if (a.mode != 0) {  // inverse layers 0 .. g-1
+        for (int r = 0; r < min(uf, g); r++) {
+            smem_layer<true>(s, g, r, mt, cval[r], a.d_val);
+            __syncthreads();
+        }
+        for (int r_lo = uf; r_lo < g; r_lo += 4) {
+            const int r_hi = min(g - 1, r_lo + 3);
+            run_subpass<true>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab, a.d_shfl);
+            __syncthreads();
+        }
+    }
+    for (uint32_t i = threadIdx.x; i < tile; i += blockDim.x) {
+        const uint32_t row = i >> c, col = i & cmask;
+        a.F[base | (row << a.k_lo) | col] = s[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pointmul alone (stage entry point): C[i] = A[i] * B[i].
+__global__ void __launch_bounds__(256) k_pointmul_mt(const uint4 *__restrict__ A, const uint4 *B,
+                                                      uint4 *C, uint64_t n,
+                                                      const DevTables *__restrict__ T) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint8_t *mt = smem;
+    const uint4 *src = reinterpret_cast<const uint4 *>(T->mul8);
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) reinterpret_cast<uint4 *>(mt)[i] = __ldg(src + i);
+    __syncthreads();
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        C[i] = mt_gmul128(mt, A[i], B[i]);
+}
+
+// ===========================================================================
+// Host side: per-pass tables and pass schedules.
+
+namespace {
+
+struct PassTables {
+    uint32_t *d_val = nullptr;
+    uint32_t *d_shfl = nullptr;
+};
+
+std::mutex g_pt_mu;
+std::map<std::tuple<int, int, int, int>, PassTables> g_pt;  // (device, k_lo, g, uf)
+
+int pass_tables(int k_lo, int g, int uf, PassTables *out) {
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -3;
+    auto key = std::make_tuple(dev, k_lo, g, uf);
+    std::lock_guard<std::mutex> lk(g_pt_mu);
+    auto it = g_pt.find(key);
+    if (it != g_pt.end()) {
+        *out = it->second;
+        return 0;
+    }
+    const HostTables &H = host_tables();
+    auto s_of = [&](int k, uint64_t alpha) {
+        uint32_t r = 0;
+        for (int t = 0; t < 32; t++)
+            if ((alpha >> t) & 1) r ^= H.S[k][t];
+        return r;
+    };
+    const uint32_t nval = (1u << g) - 1;
+    std::vector<uint32_t> val(std::max<uint32_t>(nval, 1));
+    std::vector<uint32_t> shfl;
+    for (int r = 0; r < g; r++) {
+        const int k = k_lo + r;
+        const uint32_t voff = (1u << g) - (1u << (g - r));
+        for (uint32_t p = 0; p < (1u << (g - 1 - r)); p++) {
+            uint32_t d = s_of(k, (uint64_t)p << (k + 1));
+            val[voff + p] = d;
+            if (r >= uf) {
+                uint32_t t[7][32];
+                shfl_table_of(d, t);
+                shfl.insert(shfl.end(), &t[0][0], &t[0][0] + 224);
+            }
+        }
+    }
+    PassTables pt;
+    if (cudaMalloc(&pt.d_val, val.size() * 4) != cudaSuccess) return -2;
+    cudaMemcpy(pt.d_val, val.data(), val.size() * 4, cudaMemcpyHostToDevice);
+    if (!shfl.empty()) {
+        if (cudaMalloc(&pt.d_shfl, shfl.size() * 4) != cudaSuccess) return -2;
+        cudaMemcpy(pt.d_shfl, shfl.data(), shfl.size() * 4, cudaMemcpyHostToDevice);
+    }
+    if (cudaGetLastError() != cudaSuccess) return -3;
+    g_pt[key] = pt;
+    *out = pt;
+    return 0;
+}
+
+constexpr int kLocalMax = 13;   // layers in the contiguous bottom pass (2^13 x 16 B tile)
+constexpr int kGlobalMax = 8;   // layers per strided pass (2^8 rows x 32 columns)
+constexpr int kCols = 5;
+
+size_t pass_smem(int g, int c, int uf, bool needs_mt) {
+    size_t b = (size_t)16 << (g + c);
+    b += (size_t)(g - uf) * 224 * 4 + 32 * 4;
+    if (needs_mt) b += 65536;
+    return b;
+}
+
+int make_pass(int k_lo, int g, int c, int uf, int mode, int g_f, FftPassCfg *p) {
+    PassTables pt;
+    int rc = pass_tables(k_lo, g, uf, &pt);
+    if (rc) return rc;
+    p->k_lo = k_lo;
+    p->g = g;
+    p->c = c;
+    p->uf = uf;
+    p->mode = mode;
+    p->g_f = g_f;
+    p->needs_mt = (uf > 0) || mode == 2;
+    p->d_val = pt.d_val;
+    p->d_shfl = pt.d_shfl;
+    p->smem = pass_smem(g, c, uf, p->needs_mt);
+    p->threads = std::max(32, std::min(512, (1 << (g + c)) / 2));
+    return 0;
+}
+
+// Global passes covering layers [lo, hi) from the top down (forward) or
+// bottom up (inverse), at most kGlobalMax layers each, balanced.
+int global_passes(int lo, int hi, bool inverse, std::vector<FftPassCfg> &out) {
+    const int L = hi - lo;
+    if (L <= 0) return 0;
+    const int n = (L + kGlobalMax - 1) / kGlobalMax;
+    std::vector<std::pair<int, int>> chunks;  // (k_lo, g) bottom-up
+    int k = lo;
+    for (int i = 0; i < n; i++) {
+        int gi = L / n + (i < L % n ? 1 : 0);
+        chunks.push_back({k, gi});
+        k += gi;
+    }
+    if (!inverse) std::reverse(chunks.begin(), chunks.end());
+    for (auto &ch : chunks) {
+        FftPassCfg p;
+        int rc = make_pass(ch.first, ch.second, kCols, 0, inverse ? 1 : 0, ch.second, &p);
+        if (rc) return rc;
+        out.push_back(p);
+    }
+    return 0;
+}
+
+}  // namespace
+
+int plan_fft_forward(int M, int log_p, std::vector<FftPassCfg> &out) {
+    out.clear();
+    int rc = global_passes(kLocalMax, log_p, false, out);
+    if (rc) return rc;
+    const int gl = std::min(log_p, kLocalMax);
+    FftPassCfg p;
+    if ((rc = make_pass(0, gl, 0, std::min(5, gl), 0, gl, &p))) return rc;
+    out.push_back(p);
+    (void)M;
+    return 0;
+}
+
+int plan_fft_inverse(int M, std::vector<FftPassCfg> &out) {
+    out.clear();
+    const int gl = std::min(M, kLocalMax);
+    FftPassCfg p;
+    int rc = make_pass(0, gl, 0, std::min(5, gl), 1, gl, &p);
+    if (rc) return rc;
+    out.push_back(p);
+    return global_passes(kLocalMax, M, true, out);
+}
+
+int plan_fft_fused(int M, int log_p, std::vector<FftPassCfg> &fwd_global, FftPassCfg &local,
+                   std::vector<FftPassCfg> &inv_global) {
+    fwd_global.clear();
+    inv_global.clear();
+    int rc = global_passes(kLocalMax, log_p, false, fwd_global);
+    if (rc) return rc;
+    const int gl = std::min(M, kLocalMax);
+    const int gf = std::min(log_p, kLocalMax);
+    if ((rc = make_pass(0, gl, 0, std::min(5, gl), 2, gf, &local))) return rc;
+    return global_passes(kLocalMax, M, true, inv_global);
+}
+
+static bool g_attr_done = false;
+
+int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,
+                    const uint4 *FA, const DevTables *T, cudaStream_t s) {
+    if (!g_attr_done) {
+        cudaFuncSetAttribute(k_fft_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_pointmul_mt, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+        g_attr_done = true;
+    }
+    FftPassArgs a;
+    a.F = F;
+    a.g64 = g64;
+    a.pmask = P ? P - 1 : 0;
+    a.FA = FA;
+    a.T = T;
+    a.d_val = p.d_val;
+    a.d_shfl = p.d_shfl;
+    a.k_lo = p.k_lo;
+    a.g = p.g;
+    a.c = p.c;
+    a.uf = p.uf;
+    a.mode = p.mode;
+    a.g_f = p.g_f;
+    a.needs_mt = p.needs_mt;
+    const uint64_t tiles = (1ull << M) >> (p.g + p.c);
+    k_fft_pass<<<(unsigned)tiles, p.threads, p.smem, s>>>(a);
+    return 0;
+}
+
+void launch_pointmul_mt(const uint4 *A, const uint4 *B, uint4 *C, uint64_t n, const DevTables *T,
+                        cudaStream_t s) {
+    if (!g_attr_done) {
+        cudaFuncSetAttribute(k_fft_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_pointmul_mt, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+        g_attr_done = true;
+    }
+    uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 152 * 8);
+    k_pointmul_mt<<<(unsigned)std::max<uint64_t>(1, blocks), 256, 65536, s>>>(A, B, C, n, T);
+}
+
+}  // namespace gf2x

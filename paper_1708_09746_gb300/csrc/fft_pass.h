@@ -1,0 +1,53 @@
+// Fused FFT_LCH passes (fft_pass.cu): configuration and launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "gf2x_dev.cuh"
+
+namespace gf2x {
+
+// One pass: layers k_lo .. k_lo+g-1, tile of 2^g rows x 2^c columns.
+struct FftPassCfg {
+    int k_lo, g, c;
+    int uf;        // tile rows r >= uf have warp-uniform multipliers
+    int mode;      // 0 forward, 1 inverse, 2 forward + pointmul + inverse
+    int g_f;       // forward layers computed (mode 0/2): rows 0 .. g_f-1
+    bool needs_mt; // F~_{2^8} product table in shared memory
+    const uint32_t *d_val;   // per-pass multipliers d(k, prefix)
+    const uint32_t *d_shfl;  // their warp-shuffle tables (rows r >= uf)
+    size_t smem;
+    int threads;
+};
+
+struct FftPassArgs {
+    uint4 *F;
+    const uint64_t *g64;  // non-null: read changeRepr(g64[idx & pmask]) instead of F
+    uint64_t pmask;
+    const uint4 *FA;      // mode 2: the other operand's transform
+    const DevTables *T;
+    const uint32_t *d_val;
+    const uint32_t *d_shfl;
+    int k_lo, g, c, uf, mode, g_f;
+    bool needs_mt;
+};
+
+// Pass schedules.  Forward: layers [0, log_p) (the layers above log_p are
+// fan-outs).  Inverse: all M layers.  Fused: forward of the second operand,
+// its bottom pass merged with pointmul and the bottom inverse layers.
+// Return 0 or a negative status.
+int plan_fft_forward(int M, int log_p, std::vector<FftPassCfg> &out);
+int plan_fft_inverse(int M, std::vector<FftPassCfg> &out);
+int plan_fft_fused(int M, int log_p, std::vector<FftPassCfg> &fwd_global, FftPassCfg &local,
+                   std::vector<FftPassCfg> &inv_global);
+
+int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,
+                    const uint4 *FA, const DevTables *T, cudaStream_t s);
+
+void launch_pointmul_mt(const uint4 *A, const uint4 *B, uint4 *C, uint64_t n, const DevTables *T,
+                        cudaStream_t s);
+
+}  // namespace gf2x

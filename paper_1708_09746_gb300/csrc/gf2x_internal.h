@@ -33,8 +33,18 @@ struct HostTables {
     uint8_t exp8[1040];
     // mul80[x] = x * v_7 in F~_{2^8} (v_7 = 0x80 closes F~_{2^16}).
     uint8_t mul80[256];
+    // Full F~_{2^8} product table: mul8[(c << 8) | x] = c * x.
+    uint8_t mul8[65536];
+    // Warp-shuffle product tables of the basis vectors v_t, t < 32: for a
+    // multiplier c, lane l holds T_w[l] = c * (l << 5w) (w < 6) and
+    // T_6[l] = c * ((l & 3) << 30); the table of c is the XOR of the tables
+    // of v_t over the set bits t of c (linearity in c).
+    uint32_t shfl_basis[32][7][32];
 };
 const HostTables &host_tables();
+
+// Warp-shuffle product table of a multiplier c (layout [7][32]).
+void shfl_table_of(uint32_t c, uint32_t out[7][32]);
 
 // ---- BasisCvt schedule (Alg. 2 / Alg. 3) -----------------------------------
 // One level = division by the binomial x^E + x^e, E = 2^logE, e = 2^loge,

@@ -108,6 +108,28 @@ static void build(HostTables &T) {
     for (int i = 255; i <= 508; i++) T.exp8[i] = T.exp8[i - 255];
     T.log8[0] = 512;
     for (int v = 0; v < 256; v++) T.mul80[v] = (uint8_t)tower_mul64(v, 0x80, 8);
+    for (int c = 0; c < 256; c++)
+        for (int x = 0; x < 256; x++) {
+            // through the log tables: c * x = g^(log c + log x)
+            T.mul8[(c << 8) | x] = T.exp8[T.log8[c] + T.log8[x]];
+        }
+    for (int t = 0; t < 32; t++)
+        for (int l = 0; l < 32; l++) {
+            for (int w = 0; w < 6; w++)
+                T.shfl_basis[t][w][l] =
+                    (uint32_t)tower_mul64(1ull << t, (uint64_t)l << (5 * w), 32);
+            T.shfl_basis[t][6][l] = (uint32_t)tower_mul64(1ull << t, (uint64_t)(l & 3) << 30, 32);
+        }
+}
+
+void shfl_table_of(uint32_t c, uint32_t out[7][32]) {
+    const HostTables &T = host_tables();
+    for (int w = 0; w < 7; w++)
+        for (int l = 0; l < 32; l++) out[w][l] = 0;
+    for (int t = 0; t < 32; t++)
+        if ((c >> t) & 1)
+            for (int w = 0; w < 7; w++)
+                for (int l = 0; l < 32; l++) out[w][l] ^= T.shfl_basis[t][w][l];
 }
 
 const HostTables &host_tables() {

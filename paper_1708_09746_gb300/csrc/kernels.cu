@@ -103,48 +103,6 @@ __global__ void k_chrepr(const uint64_t *__restrict__ g, uint64_t pmask, uint4 *
 }
 
 // ---------------------------------------------------------------------------
-// One layer k of FFT_LCH (Alg. 1) or of its inverse.  Block b (2^(k+1)
-// entries) has multiplier c = s_k(phi(b << (k+1))); each butterfly is
-//   forward: u ^= c v; v ^= u        inverse: v ^= u; u ^= c v.
-__global__ void k_fft_layer(uint4 *F, uint64_t n_half, int k, int inverse,
-                            const DevTables *__restrict__ T) {
-    __shared__ SmemGF8 gt;
-    load_gf8(gt, &T->gf8);
-    __syncthreads();
-    const uint32_t *Sk = &T->S[k][0];
-    const uint64_t half = 1ull << k;
-    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < n_half;
-         w += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t b = w >> k, j = w & (half - 1);
-        uint64_t iu = (b << (k + 1)) | j, iv = iu | half;
-        uint32_t c = s_k_of(Sk, (uint32_t)(b << (k + 1)));
-        MulConst32 mc = prep_const32(gt, c);
-        uint4 u = F[iu], v = F[iv];
-        if (!inverse) {
-            u = xor4(u, cmul128(gt, v, mc));
-            v = xor4(v, u);
-        } else {
-            v = xor4(v, u);
-            u = xor4(u, cmul128(gt, v, mc));
-        }
-        F[iu] = u;
-        F[iv] = v;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// pointmul: C[i] = A[i] * B[i] in F~_{2^128} (Sec. 4.1.3).
-__global__ void k_pointmul(const uint4 *__restrict__ A, const uint4 *B, uint4 *C, uint64_t n,
-                           const DevTables *__restrict__ T) {
-    __shared__ SmemGF8 gt;
-    load_gf8(gt, &T->gf8);
-    __syncthreads();
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        C[i] = gmul128(gt, A[i], B[i]);
-}
-
-// ---------------------------------------------------------------------------
 // changeRepr^-1 and InterleavedCombine (Sec. 2.1): psi(F[j]) is a polynomial
 // of degree < 128 in z; z -> x and y -> x^64 add its high word into the next
 // output word.
@@ -236,25 +194,6 @@ template uint64_t run_basis_cvt<uint4>(uint4 *, int, const std::vector<Level> &,
 void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const DevTables *T,
                    cudaStream_t s) {
     k_chrepr<<<grid_for(n, 256), 256, 0, s>>>(g, P - 1, F, n, T);
-}
-
-uint64_t run_fft(uint4 *F, int log_n, int log_p, int inverse, const DevTables *T,
-                 cudaStream_t s) {
-    const uint64_t n_half = (1ull << log_n) / 2;
-    uint64_t launches = 0;
-    if (!inverse) {
-        for (int k = log_p - 1; k >= 0; k--, launches++)
-            k_fft_layer<<<grid_for(n_half, 256), 256, 0, s>>>(F, n_half, k, 0, T);
-    } else {
-        for (int k = 0; k < log_n; k++, launches++)
-            k_fft_layer<<<grid_for(n_half, 256), 256, 0, s>>>(F, n_half, k, 1, T);
-    }
-    return launches;
-}
-
-void launch_pointmul(const uint4 *A, const uint4 *B, uint4 *C, uint64_t n, const DevTables *T,
-                     cudaStream_t s) {
-    k_pointmul<<<grid_for(n, 256), 256, 0, s>>>(A, B, C, n, T);
 }
 
 void launch_ichrepr_combine(const uint4 *F, uint64_t n, uint64_t *out, uint64_t out_words,

@@ -31,11 +31,6 @@ uint64_t run_basis_cvt(T *f, int m, const std::vector<Level> &fwd, int inverse, 
 void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const DevTables *T,
                    cudaStream_t s);
 
-uint64_t run_fft(uint4 *F, int log_n, int log_p, int inverse, const DevTables *T, cudaStream_t s);
-
-void launch_pointmul(const uint4 *A, const uint4 *B, uint4 *C, uint64_t n, const DevTables *T,
-                     cudaStream_t s);
-
 void launch_ichrepr_combine(const uint4 *F, uint64_t n, uint64_t *out, uint64_t out_words,
                             uint64_t last_mask, const DevTables *T, cudaStream_t s);
 
