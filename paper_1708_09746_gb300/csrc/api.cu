@@ -64,6 +64,7 @@ int get_tables(const DevTables **out) {
             }
         std::memcpy(h->mul8, H.mul8, sizeof(H.mul8));
         std::memcpy(h->shfl_basis, H.shfl_basis, sizeof(H.shfl_basis));
+        std::memcpy(h->shfl_m4r, H.shfl_m4r, sizeof(H.shfl_m4r));
         DevTables *d = nullptr;
         if (cudaMalloc(&d, sizeof(DevTables)) != cudaSuccess) {
             cudaGetLastError();

@@ -30,6 +30,7 @@
 #include "fft_pass.h"
 #include "gf2x_internal.h"
 #include "gf2x_mul.cuh"
+#include "kernels.h"
 
 namespace gf2x {
 
@@ -148,14 +149,10 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     __syncthreads();
     for (int i = threadIdx.x; i < (g - uf) * 224; i += blockDim.x) {
         const int r = uf + i / 224, wl = i % 224;
-        uint32_t cv = cval[r], acc = 0;
-        const uint32_t *b = &a.T->shfl_basis[0][0][0] + wl;
-        while (cv) {
-            const int t = __ffs(cv) - 1;
-            acc ^= __ldg(b + t * 224);
-            cv &= cv - 1;
-        }
-        ctab[i] = acc;
+        const uint32_t cv = cval[r];
+        const uint32_t *b = &a.T->shfl_m4r[0][0][0][0] + wl;
+        ctab[i] = __ldg(b + (cv & 255) * 224) ^ __ldg(b + (256 + ((cv >> 8) & 255)) * 224) ^
+                  __ldg(b + (512 + ((cv >> 16) & 255)) * 224) ^ __ldg(b + (768 + (cv >> 24)) * 224);
     }
     if (a.needs_mt) {
         const uint4 *src = reinterpret_cast<const uint4 *>(a.T->mul8);
@@ -280,9 +277,9 @@ int pass_tables(int k_lo, int g, int uf, PassTables *out) {
     return 0;
 }
 
-constexpr int kLocalMax = 13;   // layers in the contiguous bottom pass (2^13 x 16 B tile)
-constexpr int kGlobalMax = 8;   // layers per strided pass (2^8 rows x 32 columns)
-constexpr int kCols = 5;
+constexpr int kTileLog = 13;    // every pass holds a 2^13-element tile (128 KiB)
+constexpr int kLocalMax = 13;   // layers in the contiguous bottom pass
+constexpr int kGlobalMax = 8;   // layers per strided pass (2^g rows x 2^(13-g) columns)
 
 size_t pass_smem(int g, int c, int uf, bool needs_mt) {
     size_t b = (size_t)16 << (g + c);
@@ -325,7 +322,8 @@ int global_passes(int lo, int hi, bool inverse, std::vector<FftPassCfg> &out) {
     if (!inverse) std::reverse(chunks.begin(), chunks.end());
     for (auto &ch : chunks) {
         FftPassCfg p;
-        int rc = make_pass(ch.first, ch.second, kCols, 0, inverse ? 1 : 0, ch.second, &p);
+        int rc = make_pass(ch.first, ch.second, kTileLog - ch.second, 0, inverse ? 1 : 0,
+                           ch.second, &p);
         if (rc) return rc;
         out.push_back(p);
     }
@@ -368,15 +366,9 @@ int plan_fft_fused(int M, int log_p, std::vector<FftPassCfg> &fwd_global, FftPas
     return global_passes(kLocalMax, M, true, inv_global);
 }
 
-static bool g_attr_done = false;
-
 int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,
                     const uint4 *FA, const DevTables *T, cudaStream_t s) {
-    if (!g_attr_done) {
-        cudaFuncSetAttribute(k_fft_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        cudaFuncSetAttribute(k_pointmul_mt, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
-        g_attr_done = true;
-    }
+    ensure_smem_attr(reinterpret_cast<const void *>(k_fft_pass), 227 * 1024);
     FftPassArgs a;
     a.F = F;
     a.g64 = g64;
@@ -399,11 +391,7 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
 
 void launch_pointmul_mt(const uint4 *A, const uint4 *B, uint4 *C, uint64_t n, const DevTables *T,
                         cudaStream_t s) {
-    if (!g_attr_done) {
-        cudaFuncSetAttribute(k_fft_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        cudaFuncSetAttribute(k_pointmul_mt, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
-        g_attr_done = true;
-    }
+    ensure_smem_attr(reinterpret_cast<const void *>(k_pointmul_mt), 65536);
     uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 152 * 8);
     k_pointmul_mt<<<(unsigned)std::max<uint64_t>(1, blocks), 256, 65536, s>>>(A, B, C, n, T);
 }

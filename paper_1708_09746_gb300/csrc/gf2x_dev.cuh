@@ -21,6 +21,7 @@ struct DevTables {
     uint4 chr_out[16][256];
     uint8_t mul8[65536];
     uint32_t shfl_basis[32][7][32];
+    uint32_t shfl_m4r[4][256][7][32];
 };
 
 __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) {

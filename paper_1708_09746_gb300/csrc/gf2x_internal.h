@@ -40,6 +40,10 @@ struct HostTables {
     // T_6[l] = c * ((l & 3) << 30); the table of c is the XOR of the tables
     // of v_t over the set bits t of c (linearity in c).
     uint32_t shfl_basis[32][7][32];
+    // The same tables for every byte value at each byte position p of the
+    // multiplier: shfl_m4r[p][v] = table of (v << 8p), so the table of c is
+    // the XOR of four entries (method of four Russians over c's bytes).
+    uint32_t shfl_m4r[4][256][7][32];
 };
 const HostTables &host_tables();
 

@@ -120,6 +120,15 @@ static void build(HostTables &T) {
                     (uint32_t)tower_mul64(1ull << t, (uint64_t)l << (5 * w), 32);
             T.shfl_basis[t][6][l] = (uint32_t)tower_mul64(1ull << t, (uint64_t)(l & 3) << 30, 32);
         }
+    for (int p = 0; p < 4; p++)
+        for (int v = 0; v < 256; v++)
+            for (int w = 0; w < 7; w++)
+                for (int l = 0; l < 32; l++) {
+                    uint32_t acc = 0;
+                    for (int j = 0; j < 8; j++)
+                        if ((v >> j) & 1) acc ^= T.shfl_basis[8 * p + j][w][l];
+                    T.shfl_m4r[p][v][w][l] = acc;
+                }
 }
 
 void shfl_table_of(uint32_t c, uint32_t out[7][32]) {

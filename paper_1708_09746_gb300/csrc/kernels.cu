@@ -1,6 +1,9 @@
 // CUDA kernels of the product path (Alg. 5) and their host launchers.
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
+#include <set>
+#include <tuple>
 #include <vector>
 
 #include "gf2x_dev.cuh"
@@ -66,24 +69,35 @@ __global__ void k_bcvt_level(T *f, uint64_t n_half, int logE, int loge, int inve
     }
 }
 
+// A strided tile: index bits [0, c) ("columns", consecutive in memory) and
+// [lo, lo + w) ("rows"); the other bits name the CTA.  A level whose mixing
+// bits [loge, logE] lie inside the rows acts on the tile-local index
+// (row << c) | col exactly as on the global index, with logE and loge moved
+// by c - lo (the levels in `lb` are given in tile-local form).
 template <typename T>
-__global__ void k_bcvt_tile(T *f, int tile_log, LevelBatch lb, int inverse) {
+__global__ void k_bcvt_tile(T *f, int c, int lo, int w, LevelBatch lb, int inverse) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s = reinterpret_cast<T *>(smem_raw);
-    const uint64_t tile = 1ull << tile_log;
-    T *g = f + blockIdx.x * tile;
-    for (uint64_t i = threadIdx.x; i < tile; i += blockDim.x) s[i] = g[i];
+    const uint32_t tile = 1u << (c + w);
+    const int mid_bits = lo - c;
+    const uint64_t mid = blockIdx.x & ((1ull << mid_bits) - 1);
+    const uint64_t hi = (uint64_t)blockIdx.x >> mid_bits;
+    const uint64_t base = (hi << (lo + w)) | (mid << c);
+    const uint32_t cmask = (1u << c) - 1;
+    for (uint32_t i = threadIdx.x; i < tile; i += blockDim.x)
+        s[i] = f[base | ((uint64_t)(i >> c) << lo) | (i & cmask)];
     __syncthreads();
     for (int L = 0; L < lb.count; L++) {
         const int logE = lb.logE[L], loge = lb.loge[L];
-        const uint64_t E = 1ull << logE, e = 1ull << loge;
-        for (uint64_t w = threadIdx.x; w < tile / 2; w += blockDim.x) {
-            uint64_t seg = w >> logE, t = w & (E - 1);
-            if (t < E - e) bcvt_item(s, seg << (logE + 1), E, e, t, inverse);
+        const uint32_t E = 1u << logE, e = 1u << loge;
+        for (uint32_t q = threadIdx.x; q < tile / 2; q += blockDim.x) {
+            uint32_t seg = q >> logE, t = q & (E - 1);
+            if (t < E - e) bcvt_item(s, (uint64_t)seg << (logE + 1), E, e, t, inverse);
         }
         __syncthreads();
     }
-    for (uint64_t i = threadIdx.x; i < tile; i += blockDim.x) g[i] = s[i];
+    for (uint32_t i = threadIdx.x; i < tile; i += blockDim.x)
+        f[base | ((uint64_t)(i >> c) << lo) | (i & cmask)] = s[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -139,6 +153,18 @@ __global__ void k_ichrepr_combine(const uint4 *__restrict__ F, uint64_t n, uint6
 // ===========================================================================
 // Host launchers.
 
+void ensure_smem_attr(const void *func, int bytes) {
+    static std::mutex mu;
+    static std::set<std::tuple<int, const void *, int>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_tuple(dev, func, bytes);
+    if (done.count(key)) return;
+    cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    done.insert(key);
+}
+
 static inline unsigned grid_for(uint64_t work, unsigned block, unsigned cap = 1u << 20) {
     uint64_t g = (work + block - 1) / block;
     if (g == 0) g = 1;
@@ -150,38 +176,72 @@ void launch_split_pad(const uint64_t *a, uint64_t nw, uint64_t last_mask, uint64
     k_split_pad<<<grid_for(P, 256), 256, 0, s>>>(a, nw, last_mask, w, P);
 }
 
+// Tiles of 128 KiB: 2^14 words or 2^13 128-bit elements; rows of at least
+// 128 bytes of consecutive elements when the tile is strided.
 template <typename T>
 static int tile_log_for() {
-    return sizeof(T) == 8 ? 12 : 11;  // 32 KiB tiles
+    return sizeof(T) == 8 ? 14 : 13;
+}
+template <typename T>
+static int min_cols_for() {
+    return sizeof(T) == 8 ? 4 : 3;
 }
 
+// Greedy schedule: consecutive levels whose mixing ranges [loge, logE] fit one
+// tile together (with >= min_cols low column bits, or contiguous) share one
+// pass; a level too wide for any tile is a streaming pass of its own.
 template <typename T>
 uint64_t run_basis_cvt(T *f, int m, const std::vector<Level> &fwd, int inverse, cudaStream_t s) {
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<T>),
+                     (int)(sizeof(T) << tile_log_for<T>()));
     uint64_t launches = 0;
     std::vector<Level> lv = fwd;
     if (inverse) std::reverse(lv.begin(), lv.end());
-    const int tl = std::min(tile_log_for<T>(), m);
+    const int budget = std::min(tile_log_for<T>(), m), cmin = min_cols_for<T>();
     const uint64_t n = 1ull << m;
+    auto fits = [&](int glo, int ghi) {
+        if (ghi + 1 <= budget) return true;
+        return glo >= cmin && (ghi - glo + 1) + cmin <= budget;
+    };
     size_t i = 0;
     while (i < lv.size()) {
-        if (lv[i].logE + 1 <= tl) {
-            LevelBatch lb{};
-            lb.count = 0;
-            while (i < lv.size() && lv[i].logE + 1 <= tl && lb.count < LevelBatch::kMax) {
-                lb.logE[lb.count] = lv[i].logE;
-                lb.loge[lb.count] = lv[i].loge;
-                lb.count++;
-                i++;
-            }
-            size_t smem = (size_t)sizeof(T) << tl;
-            k_bcvt_tile<T><<<(unsigned)(n >> tl), 256, smem, s>>>(f, tl, lb, inverse);
-            launches++;
-        } else {
+        int glo = lv[i].loge, ghi = lv[i].logE;
+        if (!fits(glo, ghi)) {
             k_bcvt_level<T><<<grid_for(n / 2, 256), 256, 0, s>>>(f, n / 2, lv[i].logE, lv[i].loge,
                                                                  inverse);
             launches++;
             i++;
+            continue;
         }
+        size_t j = i + 1;
+        while (j < lv.size() && (int)(j - i) < LevelBatch::kMax &&
+               fits(std::min(glo, (int)lv[j].loge), std::max(ghi, (int)lv[j].logE))) {
+            glo = std::min(glo, (int)lv[j].loge);
+            ghi = std::max(ghi, (int)lv[j].logE);
+            j++;
+        }
+        int c, lo, w;
+        if (ghi + 1 <= budget) {  // contiguous tile
+            c = 0;
+            lo = 0;
+            w = budget;
+        } else {
+            w = ghi - glo + 1;
+            c = std::min(glo, budget - w);
+            lo = glo;
+        }
+        LevelBatch lb{};
+        lb.count = 0;
+        for (size_t q = i; q < j; q++) {
+            lb.logE[lb.count] = (int8_t)(lv[q].logE - lo + c);
+            lb.loge[lb.count] = (int8_t)(lv[q].loge - lo + c);
+            lb.count++;
+        }
+        size_t smem = sizeof(T) << (c + w);
+        int threads = std::max(32, std::min(512, 1 << (c + w - 1)));
+        k_bcvt_tile<T><<<(unsigned)(n >> (c + w)), threads, smem, s>>>(f, c, lo, w, lb, inverse);
+        launches++;
+        i = j;
     }
     return launches;
 }

@@ -19,6 +19,10 @@ struct LevelBatch {
     int8_t loge[kMax];
 };
 
+// Raises the dynamic shared-memory limit of `func` to `bytes` once per device
+// (the attribute is per device context).
+void ensure_smem_attr(const void *func, int bytes);
+
 void launch_split_pad(const uint64_t *a, uint64_t nw, uint64_t last_mask, uint64_t *w, uint64_t P,
                       cudaStream_t s);
 

@@ -23,7 +23,7 @@ def _rand128(seed, n):
     return pairs_to_ints(w)
 
 
-@pytest.mark.parametrize("log_n", [0, 1, 2, 4, 7, 11, 12, 13, 14, 16])
+@pytest.mark.parametrize("log_n", [0, 1, 2, 4, 7, 11, 12, 13, 14, 16, 18, 20])
 def test_basis_cvt64(log_n):
     n = 1 << log_n
     f = W.random_words(100 + log_n, n)
@@ -36,7 +36,7 @@ def test_basis_cvt64(log_n):
     assert np.array_equal(from_dev(d, n), f)
 
 
-@pytest.mark.parametrize("log_n", [1, 3, 10, 11, 12, 13, 15])
+@pytest.mark.parametrize("log_n", [1, 3, 10, 11, 12, 13, 15, 17, 19])
 def test_basis_cvt128(log_n):
     n = 1 << log_n
     f = _rand128(200 + log_n, n)
