@@ -24,6 +24,7 @@ constexpr int kMaxLogN = 28;  // FFT points N <= 2^28
 // ---- Per-device context: the size-independent tables, uploaded once. ------
 struct DeviceCtx {
     DevTables *tables = nullptr;
+    int *status = nullptr;  // device status word of the pipelined kernels
 };
 
 std::mutex g_ctx_mu;
@@ -75,10 +76,39 @@ int get_tables(const DevTables **out) {
             cudaFree(d);
             return GF2X_ECUDA;
         }
+        int *st = nullptr;
+        if (cudaMalloc(&st, sizeof(int)) != cudaSuccess || cudaMemset(st, 0, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(d);
+            if (st) cudaFree(st);
+            return GF2X_ENOMEM;
+        }
         c.tables = d;
+        c.status = st;
     }
     *out = c.tables;
     return GF2X_OK;
+}
+
+// Device status word of the current device (valid after get_tables).
+int *device_status() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    return g_ctx[dev].status;
+}
+
+// Reads and clears the device status word (synchronises the device).
+int take_device_status() {
+    int *st = device_status();
+    if (!st) return GF2X_OK;
+    int v = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&v, st, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return GF2X_ECUDA;
+    }
+    if (v) cudaMemset(st, 0, sizeof(int));
+    return v;
 }
 
 int check_launch() {
@@ -238,24 +268,25 @@ int plan_run(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t 
     n = run_basis_cvt<uint64_t>(WA, p->pa_log, p->lv_a, 0, s);
     n += run_basis_cvt<uint64_t>(WB, p->pb_log, p->lv_b, 0, s);
     tm.end(n);
-    // changeRepr (+ fan-out of the layers above log2 P)
-    // changeRepr + FFT_LCH of a (changeRepr fused into the first pass)
+    int *st = device_status();
+    // changeRepr + FFT_LCH of a (changeRepr fused into the first pass; the
+    // layers above log2 Pa are fan-outs: the pass reads the blocks periodically)
     tm.begin(ST_FFT_A);
     for (size_t i = 0; i < p->fft_a.size(); i++)
-        launch_fft_pass(p->fft_a[i], p->M, FA, i == 0 ? WA : nullptr, p->Pa, nullptr, T, s);
+        launch_fft_pass(p->fft_a[i], p->M, FA, i == 0 ? WA : nullptr, p->Pa, nullptr, T, st, s);
     tm.end(p->fft_a.size());
     // changeRepr + FFT_LCH of b, top layers
     tm.begin(ST_FFT_B);
     for (size_t i = 0; i < p->fft_b.size(); i++)
-        launch_fft_pass(p->fft_b[i], p->M, FB, i == 0 ? WB : nullptr, p->Pb, nullptr, T, s);
+        launch_fft_pass(p->fft_b[i], p->M, FB, i == 0 ? WB : nullptr, p->Pb, nullptr, T, st, s);
     tm.end(p->fft_b.size());
     // bottom layers of FFT(b), pointmul, bottom layers of iFFT_LCH
     tm.begin(ST_FUSED);
-    launch_fft_pass(p->fused, p->M, FB, p->fft_b.empty() ? WB : nullptr, p->Pb, FA, T, s);
+    launch_fft_pass(p->fused, p->M, FB, p->fft_b.empty() ? WB : nullptr, p->Pb, FA, T, st, s);
     tm.end(1);
     // iFFT_LCH top layers, iBasisCvt
     tm.begin(ST_IFFT);
-    for (auto &ps : p->ifft_top) launch_fft_pass(ps, p->M, FB, nullptr, 0, nullptr, T, s);
+    for (auto &ps : p->ifft_top) launch_fft_pass(ps, p->M, FB, nullptr, 0, nullptr, T, st, s);
     tm.end(p->ifft_top.size());
     tm.begin(ST_IBCVT);
     n = run_basis_cvt<uint4>(FB, p->M, p->lv_c, 1, s);
@@ -374,7 +405,7 @@ int gf2x_mul(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64_t nb
         cudaGetLastError();
         return GF2X_ECUDA;
     }
-    return GF2X_OK;
+    return take_device_status();
 }
 
 int gf2x_mul_host(const uint64_t *a_host, uint64_t na_bits, const uint64_t *b_host,
@@ -577,7 +608,7 @@ int gf2x_stage_fft(uint64_t *F, int log_n, int log_p, int inverse, gf2x_stream_t
         if (rc) return rc;
         for (auto &ps : passes)
             launch_fft_pass(ps, log_n, reinterpret_cast<uint4 *>(F), nullptr, 0, nullptr, T,
-                            reinterpret_cast<cudaStream_t>(stream));
+                            device_status(), reinterpret_cast<cudaStream_t>(stream));
     } catch (...) {
         return GF2X_ECUDA;
     }

@@ -31,6 +31,7 @@
 #include "gf2x_internal.h"
 #include "gf2x_mul.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace gf2x {
 
@@ -92,7 +93,7 @@ __device__ __forceinline__ void run_subpass(int G, uint4 *s, int c, int g, int r
         case 1: reg_subpass<1, INV>(s, c, g, r_lo, uf, ctab, d_shfl); break;
         case 2: reg_subpass<2, INV>(s, c, g, r_lo, uf, ctab, d_shfl); break;
         case 3: reg_subpass<3, INV>(s, c, g, r_lo, uf, ctab, d_shfl); break;
-        default: reg_subpass<4, INV>(s, c, g, r_lo, uf, ctab, d_shfl); break;
+        default: reg_subpass<3, INV>(s, c, g, r_lo, uf, ctab, d_shfl); break;
     }
 }
 
@@ -126,81 +127,126 @@ __device__ __forceinline__ uint4 chrepr_ldg(const DevTables *__restrict__ T, uin
     return acc;
 }
 
+// Persistent kernel: each CTA walks the tiles blockIdx.x, +gridDim.x, ...
+// with two tile buffers.  While one tile is computed, the next one is being
+// loaded by bulk copies (TMA) and the previous one stored; warp 0 issues all
+// copies.  A pass whose input is the 64-bit block array (changeRepr fused into
+// the first pass) loads with ordinary loads instead.
 __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int g = a.g, c = a.c, uf = a.uf;
     const uint32_t tile = 1u << (g + c);
-    uint4 *s = reinterpret_cast<uint4 *>(smem);
-    uint32_t *ctab = reinterpret_cast<uint32_t *>(smem + 16 * (size_t)tile);  // [g-uf][7][32]
-    uint32_t *cval = ctab + (g - uf) * 224;                                   // [g]
-    uint8_t *mt = reinterpret_cast<uint8_t *>(cval + 32);                    // 64 KiB if needed
+    uint4 *const buf0 = reinterpret_cast<uint4 *>(smem);  // buffer b at buf0 + b * tile
+    uint32_t *ctab = reinterpret_cast<uint32_t *>(smem + 32 * (size_t)tile);  // [g-uf][7][32]
+    uint32_t *cval = ctab + (g - uf) * 224;                                   // [32]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(cval + 32);                 // [2]
+    uint8_t *mt = reinterpret_cast<uint8_t *>(bar + 2);                      // 64 KiB if needed
 
-    const int mid_bits = a.k_lo - c;
-    const uint32_t mid = blockIdx.x & ((1u << mid_bits) - 1);
-    const uint32_t hi = blockIdx.x >> mid_bits;
-    const uint32_t base = (hi << (a.k_lo + g)) | (mid << c);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool pipe = (a.g64 == nullptr);
+    const TileGeom G{c, a.k_lo, g, 4};
+    const uint64_t ntiles = (1ull << a.M) >> (g + c);
     const uint32_t cmask = (1u << c) - 1;
 
-    // multipliers shared by the whole CTA
-    if ((int)threadIdx.x < g) {
-        const int k = a.k_lo + threadIdx.x;
-        cval[threadIdx.x] = s_k_of(&a.T->S[k][0], hi << (a.k_lo + g));
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < (g - uf) * 224; i += blockDim.x) {
-        const int r = uf + i / 224, wl = i % 224;
-        const uint32_t cv = cval[r];
-        const uint32_t *b = &a.T->shfl_m4r[0][0][0][0] + wl;
-        ctab[i] = __ldg(b + (cv & 255) * 224) ^ __ldg(b + (256 + ((cv >> 8) & 255)) * 224) ^
-                  __ldg(b + (512 + ((cv >> 16) & 255)) * 224) ^ __ldg(b + (768 + (cv >> 24)) * 224);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (a.needs_mt) {
         const uint4 *src = reinterpret_cast<const uint4 *>(a.T->mul8);
         uint4 *dst = reinterpret_cast<uint4 *>(mt);
         for (int i = threadIdx.x; i < 4096; i += blockDim.x) dst[i] = __ldg(src + i);
     }
-    // load the tile (changeRepr on the fly when reading the 64-bit blocks)
-    for (uint32_t i = threadIdx.x; i < tile; i += blockDim.x) {
-        const uint32_t row = i >> c, col = i & cmask;
-        const uint32_t idx = base | (row << a.k_lo) | col;
-        s[i] = a.g64 ? chrepr_ldg(a.T, __ldg(a.g64 + (idx & a.pmask))) : a.F[idx];
-    }
     __syncthreads();
+    if (pipe && warp == 0 && blockIdx.x < ntiles) tile_load_issue(G, a.F, blockIdx.x, buf0, &bar[0], lane);
 
-    if (a.mode != 1) {  // forward layers g_f-1 .. 0
-        for (int r_hi = a.g_f - 1; r_hi >= uf; r_hi -= 4) {
-            const int r_lo = max(uf, r_hi - 3);
-            run_subpass<false>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab, a.d_shfl);
+    bool aborted = false, prefetched = false;
+    uint32_t i = 0;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, i++) {
+        const int b = i & 1;
+        uint4 *s = buf0 + (b ? tile : 0);
+        const uint64_t tn = t + gridDim.x;
+        bool ok = true;
+        prefetched = false;
+        if (pipe) {
+            if (warp == 0 && tn < ntiles) {
+                bulk_wait_read_all();  // the stores out of buf[b^1] have read it
+                __syncwarp();
+                tile_load_issue(G, a.F, tn, buf0 + (b ? 0 : tile), &bar[b ^ 1], lane);
+                prefetched = true;
+            }
+            ok = mbar_wait_bounded(&bar[b], (i >> 1) & 1);
+        } else {
+            if (warp == 0) bulk_wait_read_all();
             __syncthreads();
+            const uint64_t base = tile_base(G, t);
+            for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) {
+                const uint64_t idx = base | ((uint64_t)(q >> c) << a.k_lo) | (q & cmask);
+                s[q] = chrepr_ldg(a.T, __ldg(a.g64 + (idx & a.pmask)));
+            }
         }
-        for (int r = min(uf, a.g_f) - 1; r >= 0; r--) {
-            smem_layer<false>(s, g, r, mt, cval[r], a.d_val);
-            __syncthreads();
+        if (!__syncthreads_and(ok)) {
+            aborted = true;
+            break;
         }
-    }
-    if (a.mode == 2) {  // pointmul with the other operand's transform
-        for (uint32_t i = threadIdx.x; i < tile; i += blockDim.x) {
-            const uint32_t row = i >> c, col = i & cmask;
-            const uint32_t idx = base | (row << a.k_lo) | col;
-            s[i] = mt_gmul128(mt, s[i], __ldg(a.FA + idx));
+        // multipliers shared by the tile: cval[r] = s_k(phi(hi << (k_lo + g)))
+        const uint64_t hi = t >> (a.k_lo - c);
+        const uint64_t base = tile_base(G, t);
+        if ((int)threadIdx.x < g) {
+            const int k = a.k_lo + threadIdx.x;
+            cval[threadIdx.x] = s_k_of(&a.T->S[k][0], (uint32_t)(hi << (a.k_lo + g)));
         }
         __syncthreads();
-    }
-    if (a.mode != 0) {  // inverse layers 0 .. g-1
-        for (int r = 0; r < min(uf, g); r++) {
-            smem_layer<true>(s, g, r, mt, cval[r], a.d_val);
+        for (int q = threadIdx.x; q < (g - uf) * 224; q += blockDim.x) {
+            const int r = uf + q / 224, wl = q % 224;
+            const uint32_t cv = cval[r];
+            const uint32_t *tb = &a.T->shfl_m4r[0][0][0][0] + wl;
+            ctab[q] = __ldg(tb + (cv & 255) * 224) ^ __ldg(tb + (256 + ((cv >> 8) & 255)) * 224) ^
+                      __ldg(tb + (512 + ((cv >> 16) & 255)) * 224) ^
+                      __ldg(tb + (768 + (cv >> 24)) * 224);
+        }
+        __syncthreads();
+
+        if (a.mode != 1) {  // forward layers g_f-1 .. 0
+            for (int r_hi = a.g_f - 1; r_hi >= uf; r_hi -= 3) {
+                const int r_lo = max(uf, r_hi - 2);
+                run_subpass<false>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab, a.d_shfl);
+                __syncthreads();
+            }
+            for (int r = min(uf, a.g_f) - 1; r >= 0; r--) {
+                smem_layer<false>(s, g, r, mt, cval[r], a.d_val);
+                __syncthreads();
+            }
+        }
+        if (a.mode == 2) {  // pointmul with the other operand's transform
+            for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) {
+                const uint64_t idx = base | ((uint64_t)(q >> c) << a.k_lo) | (q & cmask);
+                s[q] = mt_gmul128(mt, s[q], __ldg(a.FA + idx));
+            }
             __syncthreads();
         }
-        for (int r_lo = uf; r_lo < g; r_lo += 4) {
-            const int r_hi = min(g - 1, r_lo + 3);
-            run_subpass<true>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab, a.d_shfl);
-            __syncthreads();
+        if (a.mode != 0) {  // inverse layers 0 .. g-1
+            for (int r = 0; r < min(uf, g); r++) {
+                smem_layer<true>(s, g, r, mt, cval[r], a.d_val);
+                __syncthreads();
+            }
+            for (int r_lo = uf; r_lo < g; r_lo += 3) {
+                const int r_hi = min(g - 1, r_lo + 2);
+                run_subpass<true>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab, a.d_shfl);
+                __syncthreads();
+            }
         }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (warp == 0) tile_store_issue(G, a.F, t, s, lane);
     }
-    for (uint32_t i = threadIdx.x; i < tile; i += blockDim.x) {
-        const uint32_t row = i >> c, col = i & cmask;
-        a.F[base | (row << a.k_lo) | col] = s[i];
+    if (aborted) {
+        if (threadIdx.x == 0) atomicExch(a.status, -4);  // GF2X_ETIMEOUT
+        // let a prefetch already in flight land before the CTA exits
+        if (prefetched && threadIdx.x == 0) mbar_wait_bounded(&bar[(i & 1) ^ 1], ((i + 1) >> 1) & 1);
     }
+    if (warp == 0) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -277,13 +323,13 @@ int pass_tables(int k_lo, int g, int uf, PassTables *out) {
     return 0;
 }
 
-constexpr int kTileLog = 13;    // every pass holds a 2^13-element tile (128 KiB)
-constexpr int kLocalMax = 13;   // layers in the contiguous bottom pass
+constexpr int kTileLog = 12;    // every pass holds two 2^12-element tiles (2 x 64 KiB)
+constexpr int kLocalMax = 12;   // layers in the contiguous bottom pass
 constexpr int kGlobalMax = 8;   // layers per strided pass (2^g rows x 2^(13-g) columns)
 
 size_t pass_smem(int g, int c, int uf, bool needs_mt) {
-    size_t b = (size_t)16 << (g + c);
-    b += (size_t)(g - uf) * 224 * 4 + 32 * 4;
+    size_t b = (size_t)32 << (g + c);  // two tile buffers
+    b += (size_t)(g - uf) * 224 * 4 + 32 * 4 + 16;
     if (needs_mt) b += 65536;
     return b;
 }
@@ -367,7 +413,7 @@ int plan_fft_fused(int M, int log_p, std::vector<FftPassCfg> &fwd_global, FftPas
 }
 
 int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,
-                    const uint4 *FA, const DevTables *T, cudaStream_t s) {
+                    const uint4 *FA, const DevTables *T, int *status, cudaStream_t s) {
     ensure_smem_attr(reinterpret_cast<const void *>(k_fft_pass), 227 * 1024);
     FftPassArgs a;
     a.F = F;
@@ -384,8 +430,10 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
     a.mode = p.mode;
     a.g_f = p.g_f;
     a.needs_mt = p.needs_mt;
+    a.M = M;
+    a.status = status;
     const uint64_t tiles = (1ull << M) >> (p.g + p.c);
-    k_fft_pass<<<(unsigned)tiles, p.threads, p.smem, s>>>(a);
+    k_fft_pass<<<(unsigned)std::min<uint64_t>(tiles, num_sms()), p.threads, p.smem, s>>>(a);
     return 0;
 }
 

@@ -33,6 +33,8 @@ struct FftPassArgs {
     const uint32_t *d_shfl;
     int k_lo, g, c, uf, mode, g_f;
     bool needs_mt;
+    int M;        // log2 of the transform length
+    int *status;  // device status word (a bounded wait that ran out stores GF2X_ETIMEOUT)
 };
 
 // Pass schedules.  Forward: layers [0, log_p) (the layers above log_p are
@@ -45,7 +47,7 @@ int plan_fft_fused(int M, int log_p, std::vector<FftPassCfg> &fwd_global, FftPas
                    std::vector<FftPassCfg> &inv_global);
 
 int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,
-                    const uint4 *FA, const DevTables *T, cudaStream_t s);
+                    const uint4 *FA, const DevTables *T, int *status, cudaStream_t s);
 
 void launch_pointmul_mt(const uint4 *A, const uint4 *B, uint4 *C, uint64_t n, const DevTables *T,
                         cudaStream_t s);

@@ -1,6 +1,7 @@
 // CUDA kernels of the product path (Alg. 5) and their host launchers.
 #include <algorithm>
 #include <cstdio>
+#include <map>
 #include <mutex>
 #include <set>
 #include <tuple>
@@ -163,6 +164,21 @@ void ensure_smem_attr(const void *func, int bytes) {
     if (done.count(key)) return;
     cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     done.insert(key);
+}
+
+unsigned num_sms() {
+    static std::mutex mu;
+    static std::map<int, unsigned> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    unsigned v = n > 0 ? (unsigned)n : 1u;
+    cache[dev] = v;
+    return v;
 }
 
 static inline unsigned grid_for(uint64_t work, unsigned block, unsigned cap = 1u << 20) {

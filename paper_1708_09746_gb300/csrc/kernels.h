@@ -23,6 +23,10 @@ struct LevelBatch {
 // (the attribute is per device context).
 void ensure_smem_attr(const void *func, int bytes);
 
+// Streaming multiprocessors of the current device (grid size of the
+// persistent kernels).
+unsigned num_sms();
+
 void launch_split_pad(const uint64_t *a, uint64_t nw, uint64_t last_mask, uint64_t *w, uint64_t P,
                       cudaStream_t s);
 
