@@ -14,12 +14,11 @@
 #include "gf2x_internal.h"
 #include "fft_pass.h"
 #include "kernels.h"
+#include "plan.h"
 
 using namespace gf2x;
 
 namespace {
-
-constexpr int kMaxLogN = 28;  // FFT points N <= 2^28
 
 // ---- Per-device context: the size-independent tables, uploaded once. ------
 struct DeviceCtx {
@@ -46,26 +45,9 @@ int get_tables(const DevTables **out) {
     std::lock_guard<std::mutex> lk(g_ctx_mu);
     DeviceCtx &c = g_ctx[dev];
     if (!c.tables) {
-        const HostTables &H = host_tables();
         std::unique_ptr<DevTables> h(new (std::nothrow) DevTables);
         if (!h) return GF2X_ENOMEM;
-        static_assert(sizeof(h->S) == sizeof(H.S), "S layout");
-        std::memcpy(h->S, H.S, sizeof(H.S));
-        for (int p = 0; p < 8; p++)
-            for (int v = 0; v < 256; v++) {
-                const u128 &x = H.chr_in[p][v];
-                h->chr_in[p][v] = make_uint4((uint32_t)x.lo, (uint32_t)(x.lo >> 32),
-                                             (uint32_t)x.hi, (uint32_t)(x.hi >> 32));
-            }
-        for (int p = 0; p < 16; p++)
-            for (int v = 0; v < 256; v++) {
-                const u128 &x = H.chr_out[p][v];
-                h->chr_out[p][v] = make_uint4((uint32_t)x.lo, (uint32_t)(x.lo >> 32),
-                                              (uint32_t)x.hi, (uint32_t)(x.hi >> 32));
-            }
-        std::memcpy(h->mul8, H.mul8, sizeof(H.mul8));
-        std::memcpy(h->shfl_basis, H.shfl_basis, sizeof(H.shfl_basis));
-        std::memcpy(h->shfl_m4r, H.shfl_m4r, sizeof(H.shfl_m4r));
+        fill_dev_tables(h.get());
         DevTables *d = nullptr;
         if (cudaMalloc(&d, sizeof(DevTables)) != cudaSuccess) {
             cudaGetLastError();
@@ -136,19 +118,11 @@ bool overlap(const void *a, size_t na, const void *b, size_t nb) {
     return x < y + nb && y < x + na;
 }
 
-uint64_t words_of(uint64_t bits) { return (bits + 63) / 64; }
-
-int log2_ceil(uint64_t n) {
-    int l = 0;
-    while ((1ull << l) < n) l++;
-    return l;
-}
 
 // ---- Per-stage timing (the component profile of Table 4) -------------------
 // When enabled, plan_run records a CUDA event before and after each stage on
 // the stream it runs on; gf2x_profile_read waits for the events and sums the
 // elapsed times per stage.
-enum Stage { ST_SPLIT, ST_BCVT, ST_FFT_A, ST_FFT_B, ST_FUSED, ST_IFFT, ST_IBCVT, ST_OUT, ST_COUNT };
 const char *kStageNames[ST_COUNT] = {"split",        "basis_cvt",      "chrepr_fft_a",
                                      "chrepr_fft_b", "fft_pointmul_ifft_bottom", "ifft_top",
                                      "ibasis_cvt",   "ichrepr_combine"};
@@ -165,7 +139,7 @@ double g_prof_ms[ST_COUNT];
 uint64_t g_prof_launches[ST_COUNT];
 uint64_t g_prof_calls[ST_COUNT];
 
-struct StageTimer {
+struct StageTimer : StageHook {
     cudaStream_t s;
     bool on;
     int stage = -1;
@@ -174,13 +148,13 @@ struct StageTimer {
         std::lock_guard<std::mutex> lk(g_prof_mu);
         on = g_prof_on;
     }
-    void begin(int st) {
+    void begin(int st) override {
         if (!on) return;
         stage = st;
         cudaEventCreate(&a);
         cudaEventRecord(a, s);
     }
-    void end(uint64_t launches) {
+    void end(uint64_t launches) override {
         if (!on || stage < 0) return;
         cudaEvent_t b;
         cudaEventCreate(&b);
@@ -194,108 +168,24 @@ struct StageTimer {
 }  // namespace
 
 // ---- Plans ------------------------------------------------------------------
-struct gf2x_plan {
-    uint64_t na_bits, nb_bits, na_w, nb_w, out_words, total_bits;
-    int M, pa_log, pb_log;
-    uint64_t N, Pa, Pb;
-    std::vector<Level> lv_a, lv_b, lv_c;
-    // FFT pass schedules: forward of a; forward of b whose bottom pass also
-    // does pointmul and the bottom inverse layers; the inverse top layers.
-    std::vector<FftPassCfg> fft_a, fft_b, ifft_top;
-    FftPassCfg fused;
-    // workspace layout (bytes): FA | FB | WA | WB
-    size_t off_fa, off_fb, off_wa, off_wb, ws_bytes;
-    int device;
-    std::mutex mu;
-    void *owned_ws = nullptr;
-};
-
 namespace {
 
 int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits) {
-    p->na_bits = na_bits;
-    p->nb_bits = nb_bits;
-    p->na_w = words_of(na_bits);
-    p->nb_w = words_of(nb_bits);
-    p->total_bits = na_bits + nb_bits - 1;
-    p->out_words = words_of(p->total_bits);
-    uint64_t need = std::max<uint64_t>(2, p->na_w + p->nb_w - 1);
-    p->M = log2_ceil(need);
-    if (p->M > kMaxLogN) return GF2X_EINVAL;
-    p->N = 1ull << p->M;
-    p->pa_log = log2_ceil(p->na_w);
-    p->pb_log = log2_ceil(p->nb_w);
-    p->Pa = 1ull << p->pa_log;
-    p->Pb = 1ull << p->pb_log;
-    p->lv_a = basis_cvt_levels(p->pa_log);
-    p->lv_b = basis_cvt_levels(p->pb_log);
-    p->lv_c = basis_cvt_levels(p->M);
-    int rc = plan_fft_forward(p->M, p->pa_log, p->fft_a);
-    if (rc) return rc;
-    if ((rc = plan_fft_fused(p->M, p->pb_log, p->fft_b, p->fused, p->ifft_top))) return rc;
-    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    p->off_fa = 0;
-    p->off_fb = up(p->off_fa + 16 * p->N);
-    p->off_wa = up(p->off_fb + 16 * p->N);
-    p->off_wb = up(p->off_wa + 8 * p->Pa);
-    p->ws_bytes = up(p->off_wb + 8 * p->Pb);
-    return current_device(&p->device);
+    int rc = gf2x::plan_init(p, na_bits, nb_bits, nullptr);
+    if (rc == -1) return GF2X_EINVAL;
+    if (rc == -2) return GF2X_ENOMEM;
+    return rc ? GF2X_ECUDA : GF2X_OK;
 }
 
-// Alg. 5, stage after stage, on `s`.
+// Alg. 5, stage after stage, on `s`, with the library's tables.
 int plan_run(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out, void *ws,
              cudaStream_t s) {
     const DevTables *T;
     int rc = get_tables(&T);
     if (rc) return rc;
-    char *base = static_cast<char *>(ws);
-    uint4 *FA = reinterpret_cast<uint4 *>(base + p->off_fa);
-    uint4 *FB = reinterpret_cast<uint4 *>(base + p->off_fb);
-    uint64_t *WA = reinterpret_cast<uint64_t *>(base + p->off_wa);
-    uint64_t *WB = reinterpret_cast<uint64_t *>(base + p->off_wb);
-    auto mask_of = [](uint64_t bits) {
-        return (bits % 64) ? ((1ull << (bits % 64)) - 1) : ~0ull;
-    };
     StageTimer tm(s);
-    uint64_t n;
-    // Split
-    tm.begin(ST_SPLIT);
-    launch_split_pad(a, p->na_w, mask_of(p->na_bits), WA, p->Pa, s);
-    launch_split_pad(b, p->nb_w, mask_of(p->nb_bits), WB, p->Pb, s);
-    tm.end(2);
-    // BasisCvt on the 64-bit blocks
-    tm.begin(ST_BCVT);
-    n = run_basis_cvt<uint64_t>(WA, p->pa_log, p->lv_a, 0, s);
-    n += run_basis_cvt<uint64_t>(WB, p->pb_log, p->lv_b, 0, s);
-    tm.end(n);
-    int *st = device_status();
-    // changeRepr + FFT_LCH of a (changeRepr fused into the first pass; the
-    // layers above log2 Pa are fan-outs: the pass reads the blocks periodically)
-    tm.begin(ST_FFT_A);
-    for (size_t i = 0; i < p->fft_a.size(); i++)
-        launch_fft_pass(p->fft_a[i], p->M, FA, i == 0 ? WA : nullptr, p->Pa, nullptr, T, st, s);
-    tm.end(p->fft_a.size());
-    // changeRepr + FFT_LCH of b, top layers
-    tm.begin(ST_FFT_B);
-    for (size_t i = 0; i < p->fft_b.size(); i++)
-        launch_fft_pass(p->fft_b[i], p->M, FB, i == 0 ? WB : nullptr, p->Pb, nullptr, T, st, s);
-    tm.end(p->fft_b.size());
-    // bottom layers of FFT(b), pointmul, bottom layers of iFFT_LCH
-    tm.begin(ST_FUSED);
-    launch_fft_pass(p->fused, p->M, FB, p->fft_b.empty() ? WB : nullptr, p->Pb, FA, T, st, s);
-    tm.end(1);
-    // iFFT_LCH top layers, iBasisCvt
-    tm.begin(ST_IFFT);
-    for (auto &ps : p->ifft_top) launch_fft_pass(ps, p->M, FB, nullptr, 0, nullptr, T, st, s);
-    tm.end(p->ifft_top.size());
-    tm.begin(ST_IBCVT);
-    n = run_basis_cvt<uint4>(FB, p->M, p->lv_c, 1, s);
-    tm.end(n);
-    // changeRepr^-1 + InterleavedCombine
-    tm.begin(ST_OUT);
-    launch_ichrepr_combine(FB, p->N, out, p->out_words, mask_of(p->total_bits), T, s);
-    tm.end(1);
-    return check_launch();
+    rc = plan_run_core(p, a, b, out, ws, s, T, device_status(), &tm);
+    return rc ? GF2X_ECUDA : GF2X_OK;
 }
 
 // Plan cache for the one-shot calls, keyed by (device, sizes).
@@ -603,12 +493,12 @@ int gf2x_stage_fft(uint64_t *F, int log_n, int log_p, int inverse, gf2x_stream_t
     const DevTables *T;
     if ((rc = get_tables(&T))) return rc;
     try {
-        std::vector<FftPassCfg> passes;
+        PassList passes;
         rc = inverse ? plan_fft_inverse(log_n, passes) : plan_fft_forward(log_n, log_p, passes);
-        if (rc) return rc;
-        for (auto &ps : passes)
-            launch_fft_pass(ps, log_n, reinterpret_cast<uint4 *>(F), nullptr, 0, nullptr, T,
-                            device_status(), reinterpret_cast<cudaStream_t>(stream));
+        if (rc) return rc == -2 ? GF2X_ENOMEM : GF2X_ECUDA;
+        for (int i = 0; i < passes.n; i++)
+            launch_fft_pass(passes.v[i], log_n, reinterpret_cast<uint4 *>(F), nullptr, 0, nullptr,
+                            T, device_status(), reinterpret_cast<cudaStream_t>(stream));
     } catch (...) {
         return GF2X_ECUDA;
     }

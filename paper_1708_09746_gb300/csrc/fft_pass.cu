@@ -267,6 +267,48 @@ __global__ void __launch_bounds__(256) k_pointmul_mt(const uint4 *__restrict__ A
 // ===========================================================================
 // Host side: per-pass tables and pass schedules.
 
+void pass_tables_size(int g, int uf, size_t *n_val, size_t *n_shfl) {
+    *n_val = std::max<size_t>(((size_t)1 << g) - 1, 1);
+    size_t m = 0;
+    for (int r = uf; r < g; r++) m += (size_t)1 << (g - 1 - r);
+    *n_shfl = 224 * m;
+}
+
+void pass_tables_fill(int k_lo, int g, int uf, uint32_t *val, uint32_t *shfl) {
+    const HostTables &H = host_tables();
+    auto s_of = [&](int k, uint64_t alpha) {
+        uint32_t r = 0;
+        for (int t = 0; t < 32; t++)
+            if ((alpha >> t) & 1) r ^= H.S[k][t];
+        return r;
+    };
+    val[0] = 0;
+    size_t sh = 0;
+    for (int r = 0; r < g; r++) {
+        const int k = k_lo + r;
+        const uint32_t voff = (1u << g) - (1u << (g - r));
+        for (uint32_t p = 0; p < (1u << (g - 1 - r)); p++) {
+            const uint32_t d = s_of(k, (uint64_t)p << (k + 1));
+            val[voff + p] = d;
+            if (r >= uf) {
+                uint32_t t[7][32];
+                shfl_table_of(d, t);
+                for (int q = 0; q < 224; q++) shfl[sh + q] = (&t[0][0])[q];
+                sh += 224;
+            }
+        }
+    }
+}
+
+void pass_tables_host(int k_lo, int g, int uf, std::vector<uint32_t> &val,
+                      std::vector<uint32_t> &shfl) {
+    size_t nv, ns;
+    pass_tables_size(g, uf, &nv, &ns);
+    val.assign(nv, 0);
+    shfl.assign(ns, 0);
+    pass_tables_fill(k_lo, g, uf, val.data(), shfl.data());
+}
+
 namespace {
 
 struct PassTables {
@@ -277,55 +319,31 @@ struct PassTables {
 std::mutex g_pt_mu;
 std::map<std::tuple<int, int, int, int>, PassTables> g_pt;  // (device, k_lo, g, uf)
 
-int pass_tables(int k_lo, int g, int uf, PassTables *out) {
+// The library's own table source: built on the host once per (device, pass)
+// and kept in device allocations.
+int cached_pass_tables(int k_lo, int g, int uf, const uint32_t **d_val, const uint32_t **d_shfl) {
     int dev;
     if (cudaGetDevice(&dev) != cudaSuccess) return -3;
     auto key = std::make_tuple(dev, k_lo, g, uf);
     std::lock_guard<std::mutex> lk(g_pt_mu);
     auto it = g_pt.find(key);
-    if (it != g_pt.end()) {
-        *out = it->second;
-        return 0;
-    }
-    const HostTables &H = host_tables();
-    auto s_of = [&](int k, uint64_t alpha) {
-        uint32_t r = 0;
-        for (int t = 0; t < 32; t++)
-            if ((alpha >> t) & 1) r ^= H.S[k][t];
-        return r;
-    };
-    const uint32_t nval = (1u << g) - 1;
-    std::vector<uint32_t> val(std::max<uint32_t>(nval, 1));
-    std::vector<uint32_t> shfl;
-    for (int r = 0; r < g; r++) {
-        const int k = k_lo + r;
-        const uint32_t voff = (1u << g) - (1u << (g - r));
-        for (uint32_t p = 0; p < (1u << (g - 1 - r)); p++) {
-            uint32_t d = s_of(k, (uint64_t)p << (k + 1));
-            val[voff + p] = d;
-            if (r >= uf) {
-                uint32_t t[7][32];
-                shfl_table_of(d, t);
-                shfl.insert(shfl.end(), &t[0][0], &t[0][0] + 224);
-            }
+    if (it == g_pt.end()) {
+        std::vector<uint32_t> val, shfl;
+        pass_tables_host(k_lo, g, uf, val, shfl);
+        PassTables pt;
+        if (cudaMalloc(&pt.d_val, val.size() * 4) != cudaSuccess) return -2;
+        cudaMemcpy(pt.d_val, val.data(), val.size() * 4, cudaMemcpyHostToDevice);
+        if (!shfl.empty()) {
+            if (cudaMalloc(&pt.d_shfl, shfl.size() * 4) != cudaSuccess) return -2;
+            cudaMemcpy(pt.d_shfl, shfl.data(), shfl.size() * 4, cudaMemcpyHostToDevice);
         }
+        if (cudaGetLastError() != cudaSuccess) return -3;
+        it = g_pt.emplace(key, pt).first;
     }
-    PassTables pt;
-    if (cudaMalloc(&pt.d_val, val.size() * 4) != cudaSuccess) return -2;
-    cudaMemcpy(pt.d_val, val.data(), val.size() * 4, cudaMemcpyHostToDevice);
-    if (!shfl.empty()) {
-        if (cudaMalloc(&pt.d_shfl, shfl.size() * 4) != cudaSuccess) return -2;
-        cudaMemcpy(pt.d_shfl, shfl.data(), shfl.size() * 4, cudaMemcpyHostToDevice);
-    }
-    if (cudaGetLastError() != cudaSuccess) return -3;
-    g_pt[key] = pt;
-    *out = pt;
+    *d_val = it->second.d_val;
+    *d_shfl = it->second.d_shfl;
     return 0;
 }
-
-constexpr int kTileLog = 12;    // every pass holds two 2^12-element tiles (2 x 64 KiB)
-constexpr int kLocalMax = 12;   // layers in the contiguous bottom pass
-constexpr int kGlobalMax = 8;   // layers per strided pass (2^g rows x 2^(13-g) columns)
 
 size_t pass_smem(int g, int c, int uf, bool needs_mt) {
     size_t b = (size_t)32 << (g + c);  // two tile buffers
@@ -334,9 +352,8 @@ size_t pass_smem(int g, int c, int uf, bool needs_mt) {
     return b;
 }
 
-int make_pass(int k_lo, int g, int c, int uf, int mode, int g_f, FftPassCfg *p) {
-    PassTables pt;
-    int rc = pass_tables(k_lo, g, uf, &pt);
+int make_pass(int k_lo, int g, int c, int uf, int mode, int g_f, PassTableFn src, FftPassCfg *p) {
+    int rc = (src ? src : cached_pass_tables)(k_lo, g, uf, &p->d_val, &p->d_shfl);
     if (rc) return rc;
     p->k_lo = k_lo;
     p->g = g;
@@ -345,71 +362,79 @@ int make_pass(int k_lo, int g, int c, int uf, int mode, int g_f, FftPassCfg *p) 
     p->mode = mode;
     p->g_f = g_f;
     p->needs_mt = (uf > 0) || mode == 2;
-    p->d_val = pt.d_val;
-    p->d_shfl = pt.d_shfl;
     p->smem = pass_smem(g, c, uf, p->needs_mt);
     p->threads = std::max(32, std::min(512, (1 << (g + c)) / 2));
     return 0;
 }
 
-// Global passes covering layers [lo, hi) from the top down (forward) or
-// bottom up (inverse), at most kGlobalMax layers each, balanced.
-int global_passes(int lo, int hi, bool inverse, std::vector<FftPassCfg> &out) {
+int push_pass(PassList &out, const FftPassCfg &p) {
+    if (out.n >= PassList::kMax) return -1;
+    out.v[out.n++] = p;
+    return 0;
+}
+
+// Strided passes covering layers [lo, hi) from the top down (forward) or
+// bottom up (inverse), at most kFftGlobalMax layers each, balanced; each
+// tile is 2^g rows by 2^(12-g) columns.
+int global_passes(int lo, int hi, bool inverse, PassTableFn src, PassList &out) {
     const int L = hi - lo;
     if (L <= 0) return 0;
-    const int n = (L + kGlobalMax - 1) / kGlobalMax;
-    std::vector<std::pair<int, int>> chunks;  // (k_lo, g) bottom-up
+    const int n = (L + kFftGlobalMax - 1) / kFftGlobalMax;
+    if (n > PassList::kMax) return -1;
+    int klo[PassList::kMax], gg[PassList::kMax];
     int k = lo;
     for (int i = 0; i < n; i++) {
-        int gi = L / n + (i < L % n ? 1 : 0);
-        chunks.push_back({k, gi});
-        k += gi;
+        gg[i] = L / n + (i < L % n ? 1 : 0);
+        klo[i] = k;
+        k += gg[i];
     }
-    if (!inverse) std::reverse(chunks.begin(), chunks.end());
-    for (auto &ch : chunks) {
+    for (int q = 0; q < n; q++) {
+        const int i = inverse ? q : n - 1 - q;
         FftPassCfg p;
-        int rc = make_pass(ch.first, ch.second, kTileLog - ch.second, 0, inverse ? 1 : 0,
-                           ch.second, &p);
-        if (rc) return rc;
-        out.push_back(p);
+        int rc = make_pass(klo[i], gg[i], kFftTileLog - gg[i], 0, inverse ? 1 : 0, gg[i], src, &p);
+        if (rc || (rc = push_pass(out, p))) return rc;
     }
     return 0;
 }
 
 }  // namespace
 
-int plan_fft_forward(int M, int log_p, std::vector<FftPassCfg> &out) {
-    out.clear();
-    int rc = global_passes(kLocalMax, log_p, false, out);
+int plan_fft_forward(int M, int log_p, PassList &out, PassTableFn src) {
+    out.n = 0;
+    int rc = global_passes(kFftTileLog, log_p, false, src, out);
     if (rc) return rc;
-    const int gl = std::min(log_p, kLocalMax);
+    const int gl = std::min(log_p, kFftTileLog);
     FftPassCfg p;
-    if ((rc = make_pass(0, gl, 0, std::min(5, gl), 0, gl, &p))) return rc;
-    out.push_back(p);
+    if ((rc = make_pass(0, gl, 0, std::min(5, gl), 0, gl, src, &p))) return rc;
     (void)M;
-    return 0;
+    return push_pass(out, p);
 }
 
-int plan_fft_inverse(int M, std::vector<FftPassCfg> &out) {
-    out.clear();
-    const int gl = std::min(M, kLocalMax);
+int plan_fft_inverse(int M, PassList &out, PassTableFn src) {
+    out.n = 0;
+    const int gl = std::min(M, kFftTileLog);
     FftPassCfg p;
-    int rc = make_pass(0, gl, 0, std::min(5, gl), 1, gl, &p);
-    if (rc) return rc;
-    out.push_back(p);
-    return global_passes(kLocalMax, M, true, out);
+    int rc = make_pass(0, gl, 0, std::min(5, gl), 1, gl, src, &p);
+    if (rc || (rc = push_pass(out, p))) return rc;
+    return global_passes(kFftTileLog, M, true, src, out);
 }
 
-int plan_fft_fused(int M, int log_p, std::vector<FftPassCfg> &fwd_global, FftPassCfg &local,
-                   std::vector<FftPassCfg> &inv_global) {
-    fwd_global.clear();
-    inv_global.clear();
-    int rc = global_passes(kLocalMax, log_p, false, fwd_global);
+int plan_fft_fused(int M, int log_p, PassList &fwd_global, FftPassCfg &local, PassList &inv_global,
+                   PassTableFn src) {
+    fwd_global.n = 0;
+    inv_global.n = 0;
+    int rc = global_passes(kFftTileLog, log_p, false, src, fwd_global);
     if (rc) return rc;
-    const int gl = std::min(M, kLocalMax);
-    const int gf = std::min(log_p, kLocalMax);
-    if ((rc = make_pass(0, gl, 0, std::min(5, gl), 2, gf, &local))) return rc;
-    return global_passes(kLocalMax, M, true, inv_global);
+    const int gl = std::min(M, kFftTileLog);
+    const int gf = std::min(log_p, kFftTileLog);
+    if ((rc = make_pass(0, gl, 0, std::min(5, gl), 2, gf, src, &local))) return rc;
+    return global_passes(kFftTileLog, M, true, src, inv_global);
+}
+
+void prepare_fft_attributes() {
+    ensure_smem_attr(reinterpret_cast<const void *>(k_fft_pass), 227 * 1024);
+    ensure_smem_attr(reinterpret_cast<const void *>(k_pointmul_mt), 65536);
+    num_sms();
 }
 
 int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,

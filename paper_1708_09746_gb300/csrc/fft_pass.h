@@ -37,14 +37,40 @@ struct FftPassArgs {
     int *status;  // device status word (a bounded wait that ran out stores GF2X_ETIMEOUT)
 };
 
+// A fixed-capacity list of passes (no heap allocation).
+struct PassList {
+    static constexpr int kMax = 8;
+    int n = 0;
+    FftPassCfg v[kMax];
+};
+
+// Source of the per-pass device tables d(k, prefix) and their shuffle tables
+// for a pass (k_lo, g, uf): fills the two device pointers, returns 0 or a
+// negative status.  nullptr = the library's own cache (device allocations).
+typedef int (*PassTableFn)(int k_lo, int g, int uf, const uint32_t **d_val,
+                           const uint32_t **d_shfl);
+
+// Host copy of the tables of pass (k_lo, g, uf): d_val has 2^g - 1 entries,
+// d_shfl 224 words per multiplier of the rows r >= uf.
+void pass_tables_host(int k_lo, int g, int uf, std::vector<uint32_t> &d_val,
+                      std::vector<uint32_t> &d_shfl);
+// Words of the two tables of pass (k_lo, g, uf), and a fill into caller
+// storage of exactly those sizes (no allocation).
+void pass_tables_size(int g, int uf, size_t *n_val, size_t *n_shfl);
+void pass_tables_fill(int k_lo, int g, int uf, uint32_t *val, uint32_t *shfl);
+
 // Pass schedules.  Forward: layers [0, log_p) (the layers above log_p are
 // fan-outs).  Inverse: all M layers.  Fused: forward of the second operand,
 // its bottom pass merged with pointmul and the bottom inverse layers.
 // Return 0 or a negative status.
-int plan_fft_forward(int M, int log_p, std::vector<FftPassCfg> &out);
-int plan_fft_inverse(int M, std::vector<FftPassCfg> &out);
-int plan_fft_fused(int M, int log_p, std::vector<FftPassCfg> &fwd_global, FftPassCfg &local,
-                   std::vector<FftPassCfg> &inv_global);
+int plan_fft_forward(int M, int log_p, PassList &out, PassTableFn src = nullptr);
+int plan_fft_inverse(int M, PassList &out, PassTableFn src = nullptr);
+int plan_fft_fused(int M, int log_p, PassList &fwd_global, FftPassCfg &local, PassList &inv_global,
+                   PassTableFn src = nullptr);
+
+// Layers of the contiguous bottom pass and of each strided pass.
+constexpr int kFftTileLog = 12;
+constexpr int kFftGlobalMax = 8;
 
 int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,
                     const uint4 *FA, const DevTables *T, int *status, cudaStream_t s);

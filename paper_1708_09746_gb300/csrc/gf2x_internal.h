@@ -56,7 +56,16 @@ void shfl_table_of(uint32_t c, uint32_t out[7][32]);
 struct Level {
     int8_t logE, loge;
 };
+// A fixed-capacity list of levels (no heap allocation).
+struct LevelList {
+    static constexpr int kMax = 128;
+    int n = 0;
+    Level v[kMax];
+    void push(Level l) {
+        if (n < kMax) v[n++] = l;
+    }
+};
 // Levels of BasisCvt on 2^m coefficients, in the forward order.
-std::vector<Level> basis_cvt_levels(int m);
+LevelList basis_cvt_levels(int m);
 
 }  // namespace gf2x

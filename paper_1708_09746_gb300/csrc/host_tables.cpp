@@ -152,18 +152,18 @@ const HostTables &host_tables() {
 // largest power of two <= m-1; VarSubs divides by y^(2^j) = x^E + x^e from
 // the top (E = 2^a, e = 2^(a-K), a = m-1 .. K); then BasisCvt over y (the
 // blocks of 2^K coefficients as coefficients) and over each block.
-static void levels_rec(int m, int scale_log, std::vector<Level> &out) {
+static void levels_rec(int m, int scale_log, LevelList &out) {
     if (m <= 1) return;
     int K = 1;
     while (2 * K <= m - 1) K *= 2;
     for (int a = m - 1; a >= K; a--)
-        out.push_back(Level{(int8_t)(a + scale_log), (int8_t)(a - K + scale_log)});
+        out.push(Level{(int8_t)(a + scale_log), (int8_t)(a - K + scale_log)});
     levels_rec(m - K, scale_log + K, out);
     levels_rec(K, scale_log, out);
 }
 
-std::vector<Level> basis_cvt_levels(int m) {
-    std::vector<Level> v;
+LevelList basis_cvt_levels(int m) {
+    LevelList v;
     levels_rec(m, 0, v);
     return v;
 }

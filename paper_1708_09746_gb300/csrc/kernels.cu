@@ -207,12 +207,12 @@ static int min_cols_for() {
 // tile together (with >= min_cols low column bits, or contiguous) share one
 // pass; a level too wide for any tile is a streaming pass of its own.
 template <typename T>
-uint64_t run_basis_cvt(T *f, int m, const std::vector<Level> &fwd, int inverse, cudaStream_t s) {
+uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStream_t s) {
     ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<T>),
                      (int)(sizeof(T) << tile_log_for<T>()));
     uint64_t launches = 0;
-    std::vector<Level> lv = fwd;
-    if (inverse) std::reverse(lv.begin(), lv.end());
+    LevelList lv;
+    for (int q = 0; q < fwd.n; q++) lv.push(fwd.v[inverse ? fwd.n - 1 - q : q]);
     const int budget = std::min(tile_log_for<T>(), m), cmin = min_cols_for<T>();
     const uint64_t n = 1ull << m;
     auto fits = [&](int glo, int ghi) {
@@ -220,20 +220,20 @@ uint64_t run_basis_cvt(T *f, int m, const std::vector<Level> &fwd, int inverse, 
         return glo >= cmin && (ghi - glo + 1) + cmin <= budget;
     };
     size_t i = 0;
-    while (i < lv.size()) {
-        int glo = lv[i].loge, ghi = lv[i].logE;
+    while (i < (size_t)lv.n) {
+        int glo = lv.v[i].loge, ghi = lv.v[i].logE;
         if (!fits(glo, ghi)) {
-            k_bcvt_level<T><<<grid_for(n / 2, 256), 256, 0, s>>>(f, n / 2, lv[i].logE, lv[i].loge,
+            k_bcvt_level<T><<<grid_for(n / 2, 256), 256, 0, s>>>(f, n / 2, lv.v[i].logE, lv.v[i].loge,
                                                                  inverse);
             launches++;
             i++;
             continue;
         }
         size_t j = i + 1;
-        while (j < lv.size() && (int)(j - i) < LevelBatch::kMax &&
-               fits(std::min(glo, (int)lv[j].loge), std::max(ghi, (int)lv[j].logE))) {
-            glo = std::min(glo, (int)lv[j].loge);
-            ghi = std::max(ghi, (int)lv[j].logE);
+        while (j < (size_t)lv.n && (int)(j - i) < LevelBatch::kMax &&
+               fits(std::min(glo, (int)lv.v[j].loge), std::max(ghi, (int)lv.v[j].logE))) {
+            glo = std::min(glo, (int)lv.v[j].loge);
+            ghi = std::max(ghi, (int)lv.v[j].logE);
             j++;
         }
         int c, lo, w;
@@ -249,8 +249,8 @@ uint64_t run_basis_cvt(T *f, int m, const std::vector<Level> &fwd, int inverse, 
         LevelBatch lb{};
         lb.count = 0;
         for (size_t q = i; q < j; q++) {
-            lb.logE[lb.count] = (int8_t)(lv[q].logE - lo + c);
-            lb.loge[lb.count] = (int8_t)(lv[q].loge - lo + c);
+            lb.logE[lb.count] = (int8_t)(lv.v[q].logE - lo + c);
+            lb.loge[lb.count] = (int8_t)(lv.v[q].loge - lo + c);
             lb.count++;
         }
         size_t smem = sizeof(T) << (c + w);
@@ -262,10 +262,16 @@ uint64_t run_basis_cvt(T *f, int m, const std::vector<Level> &fwd, int inverse, 
     return launches;
 }
 
-template uint64_t run_basis_cvt<uint64_t>(uint64_t *, int, const std::vector<Level> &, int,
-                                          cudaStream_t);
-template uint64_t run_basis_cvt<uint4>(uint4 *, int, const std::vector<Level> &, int,
-                                       cudaStream_t);
+void prepare_bcvt_attributes() {
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint64_t>),
+                     (int)(sizeof(uint64_t) << tile_log_for<uint64_t>()));
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint4>),
+                     (int)(sizeof(uint4) << tile_log_for<uint4>()));
+    num_sms();
+}
+
+template uint64_t run_basis_cvt<uint64_t>(uint64_t *, int, const LevelList &, int, cudaStream_t);
+template uint64_t run_basis_cvt<uint4>(uint4 *, int, const LevelList &, int, cudaStream_t);
 
 void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const DevTables *T,
                    cudaStream_t s) {

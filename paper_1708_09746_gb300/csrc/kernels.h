@@ -27,6 +27,11 @@ void ensure_smem_attr(const void *func, int bytes);
 // persistent kernels).
 unsigned num_sms();
 
+// Sets, for the current device, every kernel attribute the launchers would
+// otherwise set on first use (so that later launches allocate nothing).
+void prepare_bcvt_attributes();
+void prepare_fft_attributes();
+
 void launch_split_pad(const uint64_t *a, uint64_t nw, uint64_t last_mask, uint64_t *w, uint64_t P,
                       cudaStream_t s);
 
@@ -34,7 +39,7 @@ void launch_split_pad(const uint64_t *a, uint64_t nw, uint64_t last_mask, uint64
 // type T (uint64_t or uint4), with the forward level list `fwd`.  The run_*
 // launchers return the number of kernel launches they enqueued.
 template <typename T>
-uint64_t run_basis_cvt(T *f, int m, const std::vector<Level> &fwd, int inverse, cudaStream_t s);
+uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStream_t s);
 
 void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const DevTables *T,
                    cudaStream_t s);

@@ -1,0 +1,126 @@
+// Product plans and the stage order of Alg. 5 (binPolyMul).
+#include <algorithm>
+#include <cstring>
+
+#include "kernels.h"
+#include "plan.h"
+
+namespace gf2x {
+
+void fill_dev_tables(DevTables *h) {
+    const HostTables &H = host_tables();
+    static_assert(sizeof(h->S) == sizeof(H.S), "S layout");
+    std::memcpy(h->S, H.S, sizeof(H.S));
+    for (int p = 0; p < 8; p++)
+        for (int v = 0; v < 256; v++) {
+            const u128 &x = H.chr_in[p][v];
+            h->chr_in[p][v] = make_uint4((uint32_t)x.lo, (uint32_t)(x.lo >> 32), (uint32_t)x.hi,
+                                         (uint32_t)(x.hi >> 32));
+        }
+    for (int p = 0; p < 16; p++)
+        for (int v = 0; v < 256; v++) {
+            const u128 &x = H.chr_out[p][v];
+            h->chr_out[p][v] = make_uint4((uint32_t)x.lo, (uint32_t)(x.lo >> 32), (uint32_t)x.hi,
+                                          (uint32_t)(x.hi >> 32));
+        }
+    std::memcpy(h->mul8, H.mul8, sizeof(H.mul8));
+    std::memcpy(h->shfl_basis, H.shfl_basis, sizeof(H.shfl_basis));
+    std::memcpy(h->shfl_m4r, H.shfl_m4r, sizeof(H.shfl_m4r));
+}
+
+int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits, PassTableFn src) {
+    p->na_bits = na_bits;
+    p->nb_bits = nb_bits;
+    p->na_w = words_of(na_bits);
+    p->nb_w = words_of(nb_bits);
+    p->total_bits = na_bits + nb_bits - 1;
+    p->out_words = words_of(p->total_bits);
+    // N: the smallest power of two >= na_w + nb_w - 1 (the product's number
+    // of 64-bit blocks), so that interpolation at N points is exact.
+    const uint64_t need = std::max<uint64_t>(2, p->na_w + p->nb_w - 1);
+    p->M = log2_ceil(need);
+    if (p->M > kMaxLogN) return -1;
+    p->N = 1ull << p->M;
+    p->pa_log = log2_ceil(p->na_w);
+    p->pb_log = log2_ceil(p->nb_w);
+    p->Pa = 1ull << p->pa_log;
+    p->Pb = 1ull << p->pb_log;
+    p->lv_a = basis_cvt_levels(p->pa_log);
+    p->lv_b = basis_cvt_levels(p->pb_log);
+    p->lv_c = basis_cvt_levels(p->M);
+    int rc = plan_fft_forward(p->M, p->pa_log, p->fft_a, src);
+    if (rc) return rc;
+    if ((rc = plan_fft_fused(p->M, p->pb_log, p->fft_b, p->fused, p->ifft_top, src))) return rc;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    p->off_fa = 0;
+    p->off_fb = up(p->off_fa + 16 * p->N);
+    p->off_wa = up(p->off_fb + 16 * p->N);
+    p->off_wb = up(p->off_wa + 8 * p->Pa);
+    p->ws_bytes = up(p->off_wb + 8 * p->Pb);
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        cudaGetLastError();
+        return -3;
+    }
+    return 0;
+}
+
+int plan_run_core(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out,
+                  void *ws, cudaStream_t s, const DevTables *T, int *st, StageHook *hook) {
+    char *base = static_cast<char *>(ws);
+    uint4 *FA = reinterpret_cast<uint4 *>(base + p->off_fa);
+    uint4 *FB = reinterpret_cast<uint4 *>(base + p->off_fb);
+    uint64_t *WA = reinterpret_cast<uint64_t *>(base + p->off_wa);
+    uint64_t *WB = reinterpret_cast<uint64_t *>(base + p->off_wb);
+    auto mask_of = [](uint64_t bits) {
+        return (bits % 64) ? ((1ull << (bits % 64)) - 1) : ~0ull;
+    };
+    auto begin = [&](int stage) {
+        if (hook) hook->begin(stage);
+    };
+    auto end = [&](uint64_t n) {
+        if (hook) hook->end(n);
+    };
+    uint64_t n;
+    // Split
+    begin(ST_SPLIT);
+    launch_split_pad(a, p->na_w, mask_of(p->na_bits), WA, p->Pa, s);
+    launch_split_pad(b, p->nb_w, mask_of(p->nb_bits), WB, p->Pb, s);
+    end(2);
+    // BasisCvt on the 64-bit blocks
+    begin(ST_BCVT);
+    n = run_basis_cvt<uint64_t>(WA, p->pa_log, p->lv_a, 0, s);
+    n += run_basis_cvt<uint64_t>(WB, p->pb_log, p->lv_b, 0, s);
+    end(n);
+    // changeRepr + FFT_LCH of a (changeRepr fused into the first pass; the
+    // layers above log2 Pa are fan-outs: the pass reads the blocks periodically)
+    begin(ST_FFT_A);
+    for (int i = 0; i < p->fft_a.n; i++)
+        launch_fft_pass(p->fft_a.v[i], p->M, FA, i == 0 ? WA : nullptr, p->Pa, nullptr, T, st, s);
+    end(p->fft_a.n);
+    // changeRepr + FFT_LCH of b, top layers
+    begin(ST_FFT_B);
+    for (int i = 0; i < p->fft_b.n; i++)
+        launch_fft_pass(p->fft_b.v[i], p->M, FB, i == 0 ? WB : nullptr, p->Pb, nullptr, T, st, s);
+    end(p->fft_b.n);
+    // bottom layers of FFT(b), pointmul, bottom layers of iFFT_LCH
+    begin(ST_FUSED);
+    launch_fft_pass(p->fused, p->M, FB, p->fft_b.n == 0 ? WB : nullptr, p->Pb, FA, T, st, s);
+    end(1);
+    // iFFT_LCH top layers
+    begin(ST_IFFT);
+    for (int i = 0; i < p->ifft_top.n; i++)
+        launch_fft_pass(p->ifft_top.v[i], p->M, FB, nullptr, 0, nullptr, T, st, s);
+    end(p->ifft_top.n);
+    // iBasisCvt
+    begin(ST_IBCVT);
+    n = run_basis_cvt<uint4>(FB, p->M, p->lv_c, 1, s);
+    end(n);
+    // changeRepr^-1 + InterleavedCombine
+    begin(ST_OUT);
+    launch_ichrepr_combine(FB, p->N, out, p->out_words, mask_of(p->total_bits), T, s);
+    end(1);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? 0 : -3;
+}
+
+}  // namespace gf2x

@@ -1,0 +1,63 @@
+// Product plans: sizes, BasisCvt level lists, FFT pass schedules, workspace
+// layout, and the order of the stages of Alg. 5.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+
+#include "fft_pass.h"
+#include "gf2x_dev.cuh"
+#include "gf2x_internal.h"
+
+struct gf2x_plan {
+    uint64_t na_bits, nb_bits, na_w, nb_w, out_words, total_bits;
+    int M, pa_log, pb_log;
+    uint64_t N, Pa, Pb;
+    gf2x::LevelList lv_a, lv_b, lv_c;
+    // FFT pass schedules: forward of a; forward of b whose bottom pass also
+    // does pointmul and the bottom inverse layers; the inverse top layers.
+    gf2x::PassList fft_a, fft_b, ifft_top;
+    gf2x::FftPassCfg fused;
+    // workspace layout (bytes): FA | FB | WA | WB
+    size_t off_fa, off_fb, off_wa, off_wb, ws_bytes;
+    int device;
+    std::mutex mu;
+    void *owned_ws = nullptr;
+};
+
+namespace gf2x {
+
+constexpr int kMaxLogN = 28;  // FFT points N <= 2^28
+
+// Stage groups timed by the profiling hook (order of gf2x_profile_read).
+enum Stage { ST_SPLIT, ST_BCVT, ST_FFT_A, ST_FFT_B, ST_FUSED, ST_IFFT, ST_IBCVT, ST_OUT, ST_COUNT };
+
+struct StageHook {
+    virtual void begin(int stage) = 0;
+    virtual void end(uint64_t launches) = 0;
+    virtual ~StageHook() {}
+};
+
+inline uint64_t words_of(uint64_t bits) { return (bits + 63) / 64; }
+
+inline int log2_ceil(uint64_t n) {
+    int l = 0;
+    while ((1ull << l) < n) l++;
+    return l;
+}
+
+// Fills *p for operands of na_bits and nb_bits (both > 0).  `src` supplies the
+// per-pass device tables (nullptr: the library's cache).  Returns a status.
+int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits, PassTableFn src);
+
+// Enqueues the whole product on `s` with workspace `ws` (p->ws_bytes bytes,
+// 256-byte aligned), tables T and status word `status`; `hook` may be null.
+int plan_run_core(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out,
+                  void *ws, cudaStream_t s, const DevTables *T, int *status, StageHook *hook);
+
+// Host image of the size-independent device tables.
+void fill_dev_tables(DevTables *h);
+
+}  // namespace gf2x
