@@ -183,6 +183,33 @@ GF2X_API int gf2x_profile_read(int stage, double *ms, uint64_t *launches,
 /* Name of stage index `stage`, or "" if out of range. */
 GF2X_API const char *gf2x_profile_stage_name(int stage);
 
+/* ---- Allocation-free product --------------------------------------------*/
+
+/* Scratch the allocation-free product keeps in a static device array on every
+ * GPU that loads this library (until the process exits), and the largest
+ * transform it accepts: N <= 2^18 points, i.e. na_w + nb_w - 1 <= 2^18 words
+ * (for example two operands of 2^23 bits each). */
+#define GF2X_NOALLOC_SCRATCH_BYTES (16ull << 20)
+#define GF2X_NOALLOC_MAX_FFT_POINTS (1ull << 18)
+
+/* c = a * b, the same result as gf2x_mul, without allocating any device
+ * memory: for callers that cannot call cudaMalloc or any other allocator
+ * while they multiply (a service whose device memory is all handed to its own
+ * pool, a plugin whose host owns every allocation, a latency path on which an
+ * allocation would synchronise the device).  The paper has no counterpart;
+ * this is a library convenience.  a, b, out: device pointers as for gf2x_mul.
+ * The work runs on `stream` and the call waits for that stream before it
+ * returns.  The scratch lives in one file-scope device array shared by every
+ * call; calls that overlapped on the GPU would race on it, so the library
+ * runs them one at a time under a process-wide lock.  The first call on each
+ * device looks the static arrays up and copies the tables in with synchronous
+ * copies: make it before any stream capture.  Products needing more than
+ * GF2X_NOALLOC_MAX_FFT_POINTS points give GF2X_EINVAL; a bounded device wait
+ * that ran out gives GF2X_ETIMEOUT. */
+GF2X_API int gf2x_mul_noalloc(const uint64_t *a, uint64_t na_bits,
+                              const uint64_t *b, uint64_t nb_bits,
+                              uint64_t *out, gf2x_stream_t stream);
+
 /* Releases the per-device tables and cached plans of this library. */
 GF2X_API int gf2x_shutdown(void);
 

@@ -20,7 +20,8 @@ __all__ = [
     "gf2x_mul_batched", "gf2x_stage_basis_cvt64", "gf2x_stage_basis_cvt128",
     "gf2x_stage_chrepr", "gf2x_stage_fft", "gf2x_stage_pointmul",
     "gf2x_stage_ichrepr_combine", "gf2x_shutdown", "gf2x_profile_enable",
-    "gf2x_profile_reset", "gf2x_profile_read", "gf2x_profile_stage_name", "LIB_PATH",
+    "gf2x_profile_reset", "gf2x_profile_read", "gf2x_profile_stage_name", "gf2x_mul_noalloc",
+    "LIB_PATH",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -64,6 +65,7 @@ _SIGS = {
     "gf2x_profile_read": (_int, [_int, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "gf2x_profile_stage_name": (ctypes.c_char_p, [_int]),
+    "gf2x_mul_noalloc": (_int, [_vp, _u64, _vp, _u64, _vp, _vp]),
 }
 
 
@@ -133,6 +135,13 @@ def gf2x_mul_async(a, na_bits, b, nb_bits, out, stream=None):
 def gf2x_mul_host(a_host, na_bits, b_host, nb_bits, out_host, stream=None):
     _check(load().gf2x_mul_host(_ptr(a_host), na_bits, _ptr(b_host), nb_bits, _ptr(out_host),
                                 _stream(stream)), "gf2x_mul_host")
+
+
+def gf2x_mul_noalloc(a, na_bits, b, nb_bits, out, stream=None):
+    """gf2x_mul for callers that cannot allocate device memory: the scratch
+    is a static device array of the library (see include/gf2x_gb300.h)."""
+    _check(load().gf2x_mul_noalloc(_ptr(a), na_bits, _ptr(b), nb_bits, _ptr(out),
+                                   _stream(stream)), "gf2x_mul_noalloc")
 
 
 def gf2x_plan_create(na_bits, nb_bits):
