@@ -1,7 +1,7 @@
 """Benchmark: one 2^28 x 2^28-bit GF(2)[x] product per step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload c1_2^28] [--no-cpu-baseline]
+                    [--workload c1_2^28] [--no-cpu-baseline] [--no-systems]
 
 Prints ONE JSON line (rank 0).  A step is one whole product (Alg. 5: Split,
 BasisCvt, changeRepr, FFT_LCH x2, pointmul, iFFT_LCH, iBasisCvt,
@@ -12,6 +12,12 @@ The L2 is flushed (a 256 MiB write) between timed steps, outside the timed
 events.  With N > 1 (torchrun) every rank runs independent products (the
 single product does not shard: replicas only) and value = max elapsed over
 ranks / (N * K) products.
+
+Beside the headline line, `batched` measures 4096 products of log-uniform
+lengths in [2^12, 2^22] bits (one batch, CUDA-graph replay, against the same
+products one by one) and `serving` a Poisson stream of 2000 requests/s with
+lengths log-uniform in [2^10, 2^26] bits and 10% 2^24 x 2^12 pairs, through
+the continuous-batching server and a one-at-a-time server.
 
 `--impl reference` times the CPU oracle (the plain Karatsuba carry-less
 product) on the host cores on a bounded sample of the same workload, scaled to
@@ -30,6 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = ("ms per 2^28-bit GF(2)[x] product (% HBM roofline); "
           "batched products/s vs one-by-one")
 PAPER_MS_2_28 = 2302.0  # Table 2, F~_{2^128} tower row, 2^28-bit operands (Haswell)
+SHFL_PER_LIMB_MUL = 7   # warp shuffles per F~_{2^32} limb product (5-bit windows)
 
 
 def _args():
@@ -40,6 +47,9 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="c1_2^28")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-systems", action="store_true",
+                   help="skip the batched and serving measurements")
+    p.add_argument("--serve-seconds", type=float, default=3.0)
     p.add_argument("--cpu-depth", type=int, default=6,
                    help="Karatsuba depth of the CPU-baseline sample (3^d sub-products)")
     return p.parse_args()
@@ -48,12 +58,12 @@ def _args():
 def _dist_init(n):
     rank, world, local = 0, 1, 0
     if n > 1 or int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        import torch
         import torch.distributed as dist
         rank = int(os.environ.get("RANK", "0"))
         world = int(os.environ.get("WORLD_SIZE", "1"))
         local = int(os.environ.get("LOCAL_RANK", "0"))
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        import torch
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", rank=rank, world_size=world)
     return rank, world, local
@@ -159,7 +169,7 @@ def cpu_sample(a, na, b, nb, depth, reps=1):
 
 
 def run_reference(args):
-    rank, world, _ = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import workloads as W
@@ -187,6 +197,140 @@ def run_reference(args):
         "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+
+
+def fft_work(na, nb):
+    """F~_{2^32} limb products of FFT(a), FFT(b) and iFFT: 4 per butterfly,
+    N/2 butterflies per computed layer (the fan-out layers above log2 P
+    multiply by zero and are not computed)."""
+    def lg(x):
+        return max(0, (x - 1).bit_length())
+    na_w, nb_w = (na + 63) // 64, (nb + 63) // 64
+    M = lg(max(2, na_w + nb_w - 1))
+    N = 1 << M
+    return 4 * (N // 2) * (lg(na_w) + lg(nb_w) + M), N, M, lg(na_w), lg(nb_w)
+
+
+def fft_hbm_bytes(N, M, la, lb):
+    """Bytes the FFT pass kernels of one product move (tile in + tile out per
+    pass, the changeRepr passes reading 8-byte blocks, the fused pass also
+    reading the other transform)."""
+    def passes(layers):
+        return 1 + max(0, -(-(layers - 12) // 8))
+    b = 0
+    for L in (la, lb):
+        npass = passes(L)
+        b += (npass - 1) * 32 * N + (8 * N + 16 * N)  # first pass reads blocks
+    b += 16 * N                                      # fused pass reads FA
+    b += (passes(M) - 1) * 32 * N                    # inverse top passes
+    return b
+
+
+def measure_batched(G, torch, W, dev, stream):
+    """4096 products, lengths floor(2^U) with U ~ U[12, 22] per side (seed 7);
+    operands are slices of one seeded random-word pool (seed 7)."""
+    lens = W.log_uniform_lengths(7, 2 * 4096, 12, 22)
+    na = [int(x) for x in lens[0::2]]
+    nb = [int(x) for x in lens[1::2]]
+    words = [((x + 63) // 64) for x in na + nb]
+    pool_n = sum(words)
+    pool = torch.from_numpy(W.random_words(7, pool_n).view("int64")).to(dev)
+    offs, o = [], 0
+    for w in words:
+        offs.append(o)
+        o += w
+    A = [pool[offs[i]:offs[i] + words[i]] for i in range(4096)]
+    B = [pool[offs[4096 + i]:offs[4096 + i] + words[4096 + i]] for i in range(4096)]
+    outs = [torch.empty(G.gf2x_out_words(na[i], nb[i]), dtype=torch.int64, device=dev)
+            for i in range(4096)]
+    # one by one: gf2x_mul_async per product on one stream (plans cached)
+    for i in range(4096):
+        G.gf2x_mul_async(A[i], na[i], B[i], nb[i], outs[i], stream)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(4096):
+        G.gf2x_mul_async(A[i], na[i], B[i], nb[i], outs[i], stream)
+    e1.record(stream)
+    stream.synchronize()
+    t_loop = e0.elapsed_time(e1) / 1e3
+    # batched: one batch, captured once and replayed
+    batch = G.gf2x_batch_create(na, nb, 8 << 30)
+    try:
+        G.gf2x_batch_execute(batch, A, B, outs, stream)
+        stream.synchronize()
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            G.gf2x_batch_execute(batch, A, B, outs, stream)
+        e1.record(stream)
+        stream.synchronize()
+        t_batch = e0.elapsed_time(e1) / 1e3 / reps
+    finally:
+        G.gf2x_batch_destroy(batch)
+    del pool, A, B, outs
+    torch.cuda.empty_cache()
+    return {"workload": "4096 products, per-side lengths log-uniform in [2^12, 2^22] bits, "
+                        "seed 7", "products": 4096,
+            "batched_products_per_s": 4096 / t_batch,
+            "one_by_one_products_per_s": 4096 / t_loop,
+            "speedup": t_loop / t_batch, "unit": "products/s",
+            "method": "gf2x_batch_execute (shape-grouped launches, CUDA graph replay) vs "
+                      "gf2x_mul_async in a loop, device-timed"}
+
+
+def measure_serving(G, torch, W, dev, seconds):
+    """Poisson arrivals at 2000/s for `seconds` (seed 8); per-side lengths
+    floor(2^U), U ~ U[10, 26], except 10% 2^24 x 2^12 pairs; operands are
+    slices of a seeded random pool, outputs a ring of 256 buffers."""
+    import numpy as np
+    t_arr = W.poisson_arrivals(8, 2000.0, seconds)
+    n = len(t_arr)
+    lens = W.log_uniform_lengths(8, 2 * n, 10, 26)
+    pick = W.random_words(9, n)
+    na, nb = [], []
+    for i in range(n):
+        if int(pick[i]) % 10 == 0:
+            na.append(1 << 24)
+            nb.append(1 << 12)
+        else:
+            na.append(int(lens[2 * i]))
+            nb.append(int(lens[2 * i + 1]))
+    pool_words = 1 << 21  # 16 MiB: operands start at seeded offsets in it
+    pool = torch.from_numpy(W.random_words(10, 2 * pool_words).view("int64")).to(dev)
+    starts = [int(x) % pool_words for x in W.random_words(11, 2 * n)]
+    ring = 256
+    max_out = (1 << 21) + 2
+    outs = torch.empty((ring, max_out), dtype=torch.int64, device=dev)
+    res = {}
+    for label, slots, batch in (("continuous_batching", 8, 64), ("one_at_a_time", 1, 1)):
+        sv = G.gf2x_server_create(16 << 30, slots, batch)
+        try:
+            tickets = []
+            t0 = time.perf_counter()
+            for i in range(n):
+                while time.perf_counter() - t0 < t_arr[i]:
+                    pass
+                if i >= ring:
+                    G.gf2x_server_wait(sv, tickets[i - ring], 120_000_000)
+                a = pool[starts[2 * i]:starts[2 * i] + (na[i] + 63) // 64]
+                b = pool[starts[2 * i + 1]:starts[2 * i + 1] + (nb[i] + 63) // 64]
+                tickets.append(G.gf2x_server_submit(sv, a, na[i], b, nb[i], outs[i % ring]))
+            for i in range(max(0, n - ring), n):
+                G.gf2x_server_wait(sv, tickets[i], 120_000_000)
+            wall = time.perf_counter() - t0
+            p50, p99, thr, done = G.gf2x_server_stats(sv)
+            res[label] = {"p50_ms": p50, "p99_ms": p99, "throughput_per_s": thr,
+                          "completed": done, "wall_s": wall, "slots": slots,
+                          "max_batch": batch}
+        finally:
+            G.gf2x_server_destroy(sv)
+    del pool, outs
+    torch.cuda.empty_cache()
+    res["workload"] = ("Poisson 2000 req/s for %.1f s (%d requests), per-side lengths "
+                       "log-uniform in [2^10, 2^26] bits, 10%% 2^24 x 2^12, seed 8" % (seconds, n))
+    res["requests"] = n
+    return res
 
 
 def run_ours(args):
@@ -264,20 +408,27 @@ def run_ours(args):
         return
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    # dominant stage by device time; its kernels are the roofline subject
-    dom = max(stages.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_launches, _) = dom
-    # algorithmic bytes per launch of the dominant kernel: a one-layer FFT
-    # pass reads and writes the N-point array of 16-byte elements
-    per_launch_bytes = {"fft": 32 * N, "ifft": 32 * N}.get(dom_name)
-    roof = None
-    if per_launch_bytes and dom_launches:
-        avg_s = dom_ms / 1e3 / dom_launches
-        ach = per_launch_bytes / avg_s / 1e9
-        roof = {"bound": "hbm", "kernel": "k_fft_layer (%s stage)" % dom_name,
-                "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "bytes_per_launch": per_launch_bytes,
-                "avg_launch_ms": avg_s * 1e3, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    # the dominant kernel: k_fft_pass runs every FFT stage
+    fft_stages = ["chrepr_fft_a", "chrepr_fft_b", "fft_pointmul_ifft_bottom", "ifft_top"]
+    fft_ms = sum(stages[k][0] for k in fft_stages) / args.steps
+    fft_launches = sum(stages[k][1] for k in fft_stages) / args.steps
+    total_stage_ms = sum(v[0] for v in stages.values()) / args.steps
+    work, _, M, la, lb = fft_work(na, nb)
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_lmul = 152 * 32 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / SHFL_PER_LIMB_MUL
+    ach_lmul = work / (fft_ms / 1e3)
+    roof = {"bound": "alu", "kernel": "k_fft_pass (all FFT_LCH / iFFT_LCH passes)",
+            "achieved": ach_lmul / 1e9, "peak": peak_lmul / 1e9,
+            "unit": "G limb-mult/s", "frac": ach_lmul / peak_lmul, "traffic": None,
+            "work_per_launch": work / max(1, fft_launches),
+            "avg_launch_ms": fft_ms / max(1, fft_launches),
+            "share_of_step": fft_ms / max(1e-9, total_stage_ms),
+            "peak_source": "derived: 152 SMs x 32 lanes x max SM clock / 7 warp shuffles "
+                           "per F~_{2^32} limb product"}
+    fbytes = fft_hbm_bytes(N, M, la, lb)
+    roof_hbm = {"bound": "hbm", "kernel": "k_fft_pass", "achieved": fbytes / (fft_ms / 1e3) / 1e9,
+                "peak": hbm, "unit": "GB/s", "frac": fbytes / (fft_ms / 1e3) / 1e9 / hbm,
+                "bytes_per_product": fbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
     plan_bytes = 240 * N
     path_frac = plan_bytes / (ms_per_product / 1e3) / 1e9 / hbm
     launches = sum(v[1] for v in stages.values())
@@ -293,6 +444,7 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "path_hbm_roofline": {"plan_bytes": plan_bytes, "frac_of_measured_hbm": path_frac},
         "roofline": roof,
+        "roofline_hbm": roof_hbm,
         "stages_ms_per_product": {k: v[0] / args.steps for k, v in stages.items()},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(a.nbytes + b.nbytes),
                 "d2h_bytes_per_step": int(8 * ow)},
@@ -300,6 +452,15 @@ def run_ours(args):
         "clocks": clk,
         "wall_s_timed": wall,
     }
+    if not args.no_systems and world == 1:
+        try:
+            line["batched"] = measure_batched(G, torch, W, dev, stream)
+        except Exception as e:  # report, keep the headline line
+            line["batched"] = {"error": repr(e)}
+        try:
+            line["serving"] = measure_serving(G, torch, W, dev, args.serve_seconds)
+        except Exception as e:
+            line["serving"] = {"error": repr(e)}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_sample(a, na, b, nb, args.cpu_depth)
     print(json.dumps(line))

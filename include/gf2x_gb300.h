@@ -127,6 +127,57 @@ GF2X_API int gf2x_mul_batched(int count, const uint64_t *const *a,
                      const uint64_t *nb_bits, uint64_t *const *out,
                      gf2x_stream_t stream);
 
+/* A reusable batch: the size list fixed at creation, the products grouped by
+ * transform shape (log2 N, log2 Pa, log2 Pb) so that each group is one launch
+ * per kernel, a device workspace of at most mem_budget_bytes (0 = 4 GiB; a
+ * group that does not fit runs in chunks) and, after the first execution, a
+ * CUDA graph of the whole batch that later executions replay.  Host arrays of
+ * `count` sizes; zero-length products are skipped. */
+typedef struct gf2x_batch gf2x_batch; /* opaque, library-owned */
+GF2X_API int gf2x_batch_create(int count, const uint64_t *na_bits,
+                               const uint64_t *nb_bits, size_t mem_budget_bytes,
+                               gf2x_batch **out);
+GF2X_API int gf2x_batch_workspace_bytes(const gf2x_batch *batch, size_t *bytes);
+/* Runs the batch on `stream` with the products' device pointers (host arrays
+ * of `count` pointers, same order as at creation).  Asynchronous; a second
+ * execution first waits until the previous one has read its descriptors.
+ * Only null pointers are rejected here (pointer kinds are not re-checked). */
+GF2X_API int gf2x_batch_execute(gf2x_batch *batch, const uint64_t *const *a,
+                                const uint64_t *const *b, uint64_t *const *out,
+                                gf2x_stream_t stream);
+GF2X_API int gf2x_batch_destroy(gf2x_batch *batch);
+
+/* ---- Serving ----------------------------------------------------------------
+ * A server runs products submitted at any time.  A worker thread admits the
+ * queued requests in arrival order as execution slots (CUDA streams, at most
+ * max_slots) and workspace memory (one device arena of mem_budget_bytes) free
+ * up; up to max_batch queued requests of the same transform shape (1 .. 64)
+ * are admitted together as one batched launch; admitted work runs
+ * concurrently.  max_slots = max_batch = 1 gives a one-at-a-time server.
+ * Latency is measured from submission to the moment the worker sees the
+ * result complete. */
+typedef struct gf2x_server gf2x_server; /* opaque, library-owned */
+GF2X_API int gf2x_server_create(size_t mem_budget_bytes, int max_slots,
+                                int max_batch, gf2x_server **out);
+/* Queues out = a * b (device pointers, kept alive until the ticket is waited
+ * for).  GF2X_EINVAL if its workspace can never fit the arena. */
+GF2X_API int gf2x_server_submit(gf2x_server *sv, const uint64_t *a,
+                                uint64_t na_bits, const uint64_t *b,
+                                uint64_t nb_bits, uint64_t *out,
+                                uint64_t *ticket);
+/* Waits at most timeout_us for the ticket: its status, or GF2X_ETIMEOUT (the
+ * ticket stays valid and can be waited for again).  A completed ticket is
+ * consumed by the wait that returns its status. */
+GF2X_API int gf2x_server_wait(gf2x_server *sv, uint64_t ticket,
+                              uint64_t timeout_us);
+/* Latency percentiles (ms) of the completed requests and throughput (requests
+ * per second from the first submission to the last completion). */
+GF2X_API int gf2x_server_stats(gf2x_server *sv, double *p50_ms, double *p99_ms,
+                               double *throughput_per_s, uint64_t *completed);
+GF2X_API int gf2x_server_reset_stats(gf2x_server *sv);
+/* Finishes the queued and running work, then releases the server. */
+GF2X_API int gf2x_server_destroy(gf2x_server *sv);
+
 /* ---- Stage entry points (each one row of the method, for checking and
  * profiling one stage alone; all device pointers, asynchronous) ----------*/
 

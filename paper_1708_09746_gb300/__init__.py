@@ -21,7 +21,9 @@ __all__ = [
     "gf2x_stage_chrepr", "gf2x_stage_fft", "gf2x_stage_pointmul",
     "gf2x_stage_ichrepr_combine", "gf2x_shutdown", "gf2x_profile_enable",
     "gf2x_profile_reset", "gf2x_profile_read", "gf2x_profile_stage_name", "gf2x_mul_noalloc",
-    "LIB_PATH",
+    "gf2x_batch_create", "gf2x_batch_workspace_bytes", "gf2x_batch_execute", "gf2x_batch_destroy",
+    "gf2x_server_create", "gf2x_server_submit", "gf2x_server_wait", "gf2x_server_stats",
+    "gf2x_server_reset_stats", "gf2x_server_destroy", "LIB_PATH",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -66,6 +68,18 @@ _SIGS = {
                                  ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "gf2x_profile_stage_name": (ctypes.c_char_p, [_int]),
     "gf2x_mul_noalloc": (_int, [_vp, _u64, _vp, _u64, _vp, _vp]),
+    "gf2x_batch_create": (_int, [_int, _vp, _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]),
+    "gf2x_batch_workspace_bytes": (_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "gf2x_batch_execute": (_int, [_vp, _vp, _vp, _vp, _vp]),
+    "gf2x_batch_destroy": (_int, [_vp]),
+    "gf2x_server_create": (_int, [ctypes.c_size_t, _int, _int, ctypes.POINTER(_vp)]),
+    "gf2x_server_submit": (_int, [_vp, _vp, _u64, _vp, _u64, _vp, ctypes.POINTER(_u64)]),
+    "gf2x_server_wait": (_int, [_vp, _u64, _u64]),
+    "gf2x_server_stats": (_int, [_vp, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64)]),
+    "gf2x_server_reset_stats": (_int, [_vp]),
+    "gf2x_server_destroy": (_int, [_vp]),
 }
 
 
@@ -242,3 +256,75 @@ def profile_all():
             return out
         out[name] = gf2x_profile_read(i)
         i += 1
+
+
+def _u64_array(vals):
+    vals = [int(v) for v in vals]
+    return (ctypes.c_uint64 * len(vals))(*vals)
+
+
+def _ptr_array(xs):
+    return (ctypes.c_void_p * len(xs))(*[_ptr(x) for x in xs])
+
+
+def gf2x_batch_create(na_bits, nb_bits, mem_budget_bytes=0):
+    """Reusable batch for these per-product sizes; returns an opaque handle."""
+    if len(na_bits) != len(nb_bits):
+        raise ValueError("size lists differ in length")
+    h = _vp()
+    na, nb = _u64_array(na_bits), _u64_array(nb_bits)
+    _check(load().gf2x_batch_create(len(na), ctypes.cast(na, _vp), ctypes.cast(nb, _vp),
+                                    int(mem_budget_bytes), ctypes.byref(h)), "gf2x_batch_create")
+    return h.value
+
+
+def gf2x_batch_workspace_bytes(batch):
+    n = ctypes.c_size_t()
+    _check(load().gf2x_batch_workspace_bytes(batch, ctypes.byref(n)), "gf2x_batch_workspace_bytes")
+    return int(n.value)
+
+
+def gf2x_batch_execute(batch, a_list, b_list, out_list, stream=None):
+    pa, pb, po = _ptr_array(a_list), _ptr_array(b_list), _ptr_array(out_list)
+    _check(load().gf2x_batch_execute(batch, ctypes.cast(pa, _vp), ctypes.cast(pb, _vp),
+                                     ctypes.cast(po, _vp), _stream(stream)), "gf2x_batch_execute")
+
+
+def gf2x_batch_destroy(batch):
+    _check(load().gf2x_batch_destroy(batch), "gf2x_batch_destroy")
+
+
+def gf2x_server_create(mem_budget_bytes, max_slots, max_batch=64):
+    h = _vp()
+    _check(load().gf2x_server_create(int(mem_budget_bytes), int(max_slots), int(max_batch),
+                                     ctypes.byref(h)), "gf2x_server_create")
+    return h.value
+
+
+def gf2x_server_submit(server, a, na_bits, b, nb_bits, out):
+    t = ctypes.c_uint64()
+    _check(load().gf2x_server_submit(server, _ptr(a), na_bits, _ptr(b), nb_bits, _ptr(out),
+                                     ctypes.byref(t)), "gf2x_server_submit")
+    return int(t.value)
+
+
+def gf2x_server_wait(server, ticket, timeout_us):
+    """Status of the ticket (0), raises on error; GF2X_ETIMEOUT raises too."""
+    _check(load().gf2x_server_wait(server, int(ticket), int(timeout_us)), "gf2x_server_wait")
+
+
+def gf2x_server_stats(server):
+    """(p50_ms, p99_ms, throughput_per_s, completed)."""
+    p50, p99, thr = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    n = ctypes.c_uint64()
+    _check(load().gf2x_server_stats(server, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(thr),
+                                    ctypes.byref(n)), "gf2x_server_stats")
+    return float(p50.value), float(p99.value), float(thr.value), int(n.value)
+
+
+def gf2x_server_reset_stats(server):
+    _check(load().gf2x_server_reset_stats(server), "gf2x_server_reset_stats")
+
+
+def gf2x_server_destroy(server):
+    _check(load().gf2x_server_destroy(server), "gf2x_server_destroy")

@@ -14,6 +14,7 @@
 #include "gf2x_internal.h"
 #include "fft_pass.h"
 #include "kernels.h"
+#include "api_internal.h"
 #include "plan.h"
 
 using namespace gf2x;
@@ -248,6 +249,26 @@ int mul_on_stream(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64
 
 }  // namespace
 
+// Entry points shared with the batch and server modules.
+namespace gf2x {
+namespace api {
+int tables(const DevTables **T) { return get_tables(T); }
+int *status_word() { return device_status(); }
+int plan_for(uint64_t na_bits, uint64_t nb_bits, std::shared_ptr<gf2x_plan> *p) {
+    return cached_plan(na_bits, nb_bits, p);
+}
+int check_product_args(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64_t nb_bits,
+                       const uint64_t *out) {
+    return check_operands(a, na_bits, b, nb_bits, out);
+}
+StageHook *new_timer(cudaStream_t s) { return new StageTimer(s); }
+int run_one(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out, void *ws,
+            cudaStream_t s) {
+    return plan_run(p, a, b, out, ws, s);
+}
+}  // namespace api
+}  // namespace gf2x
+
 extern "C" {
 
 const char *gf2x_strerror(int status) {
@@ -408,41 +429,6 @@ int gf2x_plan_destroy(gf2x_plan *p) {
     return GF2X_OK;
 }
 
-int gf2x_mul_batched(int count, const uint64_t *const *a, const uint64_t *na_bits,
-                     const uint64_t *const *b, const uint64_t *nb_bits, uint64_t *const *out,
-                     gf2x_stream_t stream) {
-    if (count < 0) return GF2X_EINVAL;
-    if (count == 0) return GF2X_OK;
-    if (!a || !na_bits || !b || !nb_bits || !out) return GF2X_EINVAL;
-    try {
-        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-        std::vector<std::shared_ptr<gf2x_plan>> plans(count);
-        size_t ws_max = 0;
-        int rc;
-        for (int i = 0; i < count; i++) {
-            if ((rc = check_operands(a[i], na_bits[i], b[i], nb_bits[i], out[i]))) return rc;
-            if (!na_bits[i] || !nb_bits[i]) continue;
-            if ((rc = cached_plan(na_bits[i], nb_bits[i], &plans[i]))) return rc;
-            ws_max = std::max(ws_max, plans[i]->ws_bytes);
-        }
-        if (!ws_max) return GF2X_OK;
-        void *ws = nullptr;
-        if (cudaMallocAsync(&ws, ws_max, s) != cudaSuccess) {
-            cudaGetLastError();
-            return GF2X_ENOMEM;
-        }
-        rc = GF2X_OK;
-        for (int i = 0; i < count && rc == GF2X_OK; i++)
-            if (plans[i]) rc = plan_run(plans[i].get(), a[i], b[i], out[i], ws, s);
-        cudaFreeAsync(ws, s);
-        return rc;
-    } catch (const std::bad_alloc &) {
-        return GF2X_ENOMEM;
-    } catch (...) {
-        return GF2X_ECUDA;
-    }
-}
-
 // ---- Stage entry points -------------------------------------------------------
 
 int gf2x_stage_basis_cvt64(uint64_t *f, int log_n, int inverse, gf2x_stream_t stream) {
@@ -534,8 +520,8 @@ int gf2x_stage_ichrepr_combine(const uint64_t *F, uint64_t n, uint64_t *out, uin
     if (ow == 0) return GF2X_OK;
     const DevTables *T;
     if ((rc = get_tables(&T))) return rc;
-    uint64_t mask = (total_bits % 64) ? ((1ull << (total_bits % 64)) - 1) : ~0ull;
-    launch_ichrepr_combine(reinterpret_cast<const uint4 *>(F), n, out, ow, mask, T,
+    const OutputDesc d{out, ow, mask_of_bits(total_bits)};
+    launch_ichrepr_combine(reinterpret_cast<const uint4 *>(F), n, 0, d, nullptr, 1, ow, T,
                            reinterpret_cast<cudaStream_t>(stream));
     return check_launch();
 }

@@ -1,0 +1,28 @@
+// Library internals shared by api.cu, batch.cu and server.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <memory>
+
+#include "plan.h"
+
+namespace gf2x {
+namespace api {
+
+// Size-independent device tables of the current device (uploaded on first use).
+int tables(const DevTables **T);
+// Device status word of the current device (valid after tables()).
+int *status_word();
+// Cached plan for these operand sizes on the current device.
+int plan_for(uint64_t na_bits, uint64_t nb_bits, std::shared_ptr<gf2x_plan> *p);
+// Argument checks of one product (device pointers, sizes, overlap).
+int check_product_args(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64_t nb_bits,
+                       const uint64_t *out);
+// Per-stage timer feeding gf2x_profile_read (records only while profiling is on).
+StageHook *new_timer(cudaStream_t s);
+// One product with plan p and workspace ws on stream s.
+int run_one(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out, void *ws,
+            cudaStream_t s);
+
+}  // namespace api
+}  // namespace gf2x

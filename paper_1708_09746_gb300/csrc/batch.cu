@@ -1,0 +1,313 @@
+// Batched products: many products of uneven sizes in few launches.
+//
+// Products whose transforms have the same shape (log2 N, log2 Pa, log2 Pb)
+// run the same kernels with the same pass schedule; only their operand
+// lengths, masks and output lengths differ.  A batch groups its products by
+// shape; each group (in chunks that fit the memory budget) is one launch per
+// kernel, blockIdx.y (or the high bits of the persistent kernels' tile index)
+// selecting the product, whose workspace sits at a fixed stride.  Per-product
+// operand/output descriptors live in a device array.
+//
+// gf2x_batch_execute captures the whole batch once into a CUDA graph (the
+// descriptor upload from a pinned host mirror plus every launch) and replays
+// it on later calls, rewriting only the pinned descriptors.
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/gf2x_gb300.h"
+#include "api_internal.h"
+#include "kernels.h"
+#include "plan.h"
+
+using namespace gf2x;
+
+struct gf2x_batch {
+    struct Chunk {
+        std::shared_ptr<gf2x_plan> plan;
+        int first, count;  // range in the grouped order
+        uint64_t max_out_words;
+    };
+    int count = 0, device = 0;
+    std::vector<uint64_t> na, nb;
+    std::vector<int> order;  // grouped order -> product index
+    std::vector<Chunk> chunks;
+    size_t ws_bytes = 0;  // shared by all chunks (run one after another)
+    void *ws = nullptr;
+    OperandDesc *d_a = nullptr, *d_b = nullptr;
+    OutputDesc *d_out = nullptr;
+    OperandDesc *h_a = nullptr, *h_b = nullptr;  // pinned mirrors
+    OutputDesc *h_out = nullptr;
+    cudaStream_t cap = nullptr;  // private stream for capture
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    bool launched = false;
+    std::mutex mu;
+};
+
+namespace {
+
+int batch_build(gf2x_batch *B, int count, const uint64_t *na_bits, const uint64_t *nb_bits,
+                size_t mem_budget) {
+    B->count = count;
+    B->na.assign(na_bits, na_bits + count);
+    B->nb.assign(nb_bits, nb_bits + count);
+    // group by transform shape
+    std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+    for (int i = 0; i < count; i++) {
+        if (!na_bits[i] || !nb_bits[i]) continue;
+        if (na_bits[i] > (1ull << 33) || nb_bits[i] > (1ull << 33)) return GF2X_EINVAL;
+        const uint64_t na_w = words_of(na_bits[i]), nb_w = words_of(nb_bits[i]);
+        const int M = log2_ceil(std::max<uint64_t>(2, na_w + nb_w - 1));
+        if (M > kMaxLogN) return GF2X_EINVAL;
+        groups[std::make_tuple(M, log2_ceil(na_w), log2_ceil(nb_w))].push_back(i);
+    }
+    size_t max_group_bytes = 0, max_one = 0;
+    for (auto &kv : groups) {
+        std::shared_ptr<gf2x_plan> p;
+        int rc = api::plan_for(B->na[kv.second[0]], B->nb[kv.second[0]], &p);
+        if (rc) return rc;
+        max_one = std::max(max_one, p->ws_bytes);
+        max_group_bytes = std::max(max_group_bytes, p->ws_bytes * kv.second.size());
+    }
+    B->ws_bytes = std::max(max_one, std::min(max_group_bytes, mem_budget));
+    for (auto &kv : groups) {
+        std::shared_ptr<gf2x_plan> p;
+        api::plan_for(B->na[kv.second[0]], B->nb[kv.second[0]], &p);
+        const int per = (int)std::max<size_t>(
+            1, std::min<size_t>(B->ws_bytes / p->ws_bytes, 65535));
+        const std::vector<int> &idx = kv.second;
+        for (size_t c0 = 0; c0 < idx.size(); c0 += per) {
+            gf2x_batch::Chunk ch;
+            ch.plan = p;
+            ch.first = (int)B->order.size();
+            ch.count = (int)std::min<size_t>(per, idx.size() - c0);
+            ch.max_out_words = 0;
+            for (int q = 0; q < ch.count; q++) {
+                const int i = idx[c0 + q];
+                B->order.push_back(i);
+                ch.max_out_words = std::max(ch.max_out_words, gf2x_out_words(B->na[i], B->nb[i]));
+            }
+            B->chunks.push_back(ch);
+        }
+    }
+    return GF2X_OK;
+}
+
+void fill_descs(const gf2x_batch *B, const uint64_t *const *a, const uint64_t *const *b,
+                uint64_t *const *out, OperandDesc *ha, OperandDesc *hb, OutputDesc *ho) {
+    for (size_t k = 0; k < B->order.size(); k++) {
+        const int i = B->order[k];
+        ha[k] = OperandDesc{a[i], words_of(B->na[i]), mask_of_bits(B->na[i])};
+        hb[k] = OperandDesc{b[i], words_of(B->nb[i]), mask_of_bits(B->nb[i])};
+        const uint64_t tot = B->na[i] + B->nb[i] - 1;
+        ho[k] = OutputDesc{out[i], words_of(tot), mask_of_bits(tot)};
+    }
+}
+
+// Every chunk, one after another, on s (workspace reused).
+int enqueue_chunks(const gf2x_batch *B, const OperandDesc *da, const OperandDesc *db,
+                   const OutputDesc *dout, void *ws, cudaStream_t s, StageHook *hook) {
+    const DevTables *T;
+    int rc = api::tables(&T);
+    if (rc) return rc;
+    int *st = api::status_word();
+    const OperandDesc none_in{nullptr, 0, 0};
+    const OutputDesc none_out{nullptr, 0, 0};
+    for (const auto &ch : B->chunks) {
+        rc = plan_run_batch(ch.plan.get(), ch.count, da + ch.first, db + ch.first, dout + ch.first,
+                            none_in, none_in, none_out, ch.max_out_words, ws, ch.plan->ws_bytes, s,
+                            T, st, hook);
+        if (rc) return GF2X_ECUDA;
+    }
+    return GF2X_OK;
+}
+
+int check_all(int count, const uint64_t *const *a, const uint64_t *na_bits,
+              const uint64_t *const *b, const uint64_t *nb_bits, uint64_t *const *out) {
+    for (int i = 0; i < count; i++) {
+        int rc = api::check_product_args(a[i], na_bits[i], b[i], nb_bits[i], out[i]);
+        if (rc) return rc;
+    }
+    return GF2X_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gf2x_mul_batched(int count, const uint64_t *const *a, const uint64_t *na_bits,
+                     const uint64_t *const *b, const uint64_t *nb_bits, uint64_t *const *out,
+                     gf2x_stream_t stream) {
+    if (count < 0) return GF2X_EINVAL;
+    if (count == 0) return GF2X_OK;
+    if (!a || !na_bits || !b || !nb_bits || !out) return GF2X_EINVAL;
+    try {
+        int rc = check_all(count, a, na_bits, b, nb_bits, out);
+        if (rc) return rc;
+        gf2x_batch B;
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        if ((rc = batch_build(&B, count, na_bits, nb_bits, free_b / 2))) return rc;
+        if (B.order.empty()) return GF2X_OK;
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        const size_t n = B.order.size();
+        std::vector<OperandDesc> ha(n), hb(n);
+        std::vector<OutputDesc> ho(n);
+        fill_descs(&B, a, b, out, ha.data(), hb.data(), ho.data());
+        char *mem = nullptr;
+        const size_t dbytes = n * (2 * sizeof(OperandDesc) + sizeof(OutputDesc));
+        const size_t ws_off = (dbytes + 255) & ~(size_t)255;
+        if (cudaMallocAsync(reinterpret_cast<void **>(&mem), ws_off + B.ws_bytes, s) != cudaSuccess) {
+            cudaGetLastError();
+            return GF2X_ENOMEM;
+        }
+        OperandDesc *da = reinterpret_cast<OperandDesc *>(mem);
+        OperandDesc *db = da + n;
+        OutputDesc *dout = reinterpret_cast<OutputDesc *>(db + n);
+        // pageable sources: each copy has read its source when the call returns
+        cudaMemcpyAsync(da, ha.data(), n * sizeof(OperandDesc), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(db, hb.data(), n * sizeof(OperandDesc), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(dout, ho.data(), n * sizeof(OutputDesc), cudaMemcpyHostToDevice, s);
+        std::unique_ptr<StageHook> tm(api::new_timer(s));
+        rc = enqueue_chunks(&B, da, db, dout, mem + ws_off, s, tm.get());
+        cudaFreeAsync(mem, s);
+        if (rc == GF2X_OK && cudaGetLastError() != cudaSuccess) rc = GF2X_ECUDA;
+        return rc;
+    } catch (const std::bad_alloc &) {
+        return GF2X_ENOMEM;
+    } catch (...) {
+        return GF2X_ECUDA;
+    }
+}
+
+int gf2x_batch_create(int count, const uint64_t *na_bits, const uint64_t *nb_bits,
+                      size_t mem_budget_bytes, gf2x_batch **out) {
+    if (!out) return GF2X_EINVAL;
+    *out = nullptr;
+    if (count <= 0 || !na_bits || !nb_bits) return GF2X_EINVAL;
+    try {
+        std::unique_ptr<gf2x_batch> B(new gf2x_batch());
+        if (cudaGetDevice(&B->device) != cudaSuccess) {
+            cudaGetLastError();
+            return GF2X_ECUDA;
+        }
+        if (!mem_budget_bytes) mem_budget_bytes = (size_t)1 << 32;
+        int rc = batch_build(B.get(), count, na_bits, nb_bits, mem_budget_bytes);
+        if (rc) return rc;
+        const size_t n = std::max<size_t>(1, B->order.size());
+        bool ok = cudaMalloc(&B->ws, B->ws_bytes ? B->ws_bytes : 256) == cudaSuccess &&
+                  cudaMalloc(&B->d_a, n * sizeof(OperandDesc)) == cudaSuccess &&
+                  cudaMalloc(&B->d_b, n * sizeof(OperandDesc)) == cudaSuccess &&
+                  cudaMalloc(&B->d_out, n * sizeof(OutputDesc)) == cudaSuccess &&
+                  cudaMallocHost(&B->h_a, n * sizeof(OperandDesc)) == cudaSuccess &&
+                  cudaMallocHost(&B->h_b, n * sizeof(OperandDesc)) == cudaSuccess &&
+                  cudaMallocHost(&B->h_out, n * sizeof(OutputDesc)) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&B->done, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            gf2x_batch_destroy(B.release());
+            return GF2X_ENOMEM;
+        }
+        *out = B.release();
+        return GF2X_OK;
+    } catch (const std::bad_alloc &) {
+        return GF2X_ENOMEM;
+    } catch (...) {
+        return GF2X_ECUDA;
+    }
+}
+
+int gf2x_batch_workspace_bytes(const gf2x_batch *B, size_t *bytes) {
+    if (!B || !bytes) return GF2X_EINVAL;
+    *bytes = B->ws_bytes;
+    return GF2X_OK;
+}
+
+int gf2x_batch_execute(gf2x_batch *B, const uint64_t *const *a, const uint64_t *const *b,
+                       uint64_t *const *out, gf2x_stream_t stream) {
+    if (!B || !a || !b || !out) return GF2X_EINVAL;
+    try {
+        std::lock_guard<std::mutex> lk(B->mu);
+        int dev = -1;
+        cudaGetDevice(&dev);
+        if (dev != B->device) return GF2X_EINVAL;
+        // pointer kinds are not re-checked here (the graph path stays cheap)
+        for (size_t k = 0; k < B->order.size(); k++) {
+            const int i = B->order[k];
+            if (!a[i] || !b[i] || !out[i]) return GF2X_EINVAL;
+        }
+        int rc;
+        if (B->order.empty()) return GF2X_OK;
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        // the previous replay has read the pinned descriptors
+        if (B->launched && cudaEventSynchronize(B->done) != cudaSuccess) {
+            cudaGetLastError();
+            return GF2X_ECUDA;
+        }
+        fill_descs(B, a, b, out, B->h_a, B->h_b, B->h_out);
+        if (!B->exec) {
+            const DevTables *T;
+            if ((rc = api::tables(&T))) return rc;
+            prepare_bcvt_attributes();
+            prepare_fft_attributes();
+            const size_t n = B->order.size();
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                cudaGetLastError();
+                return GF2X_ECUDA;
+            }
+            cudaMemcpyAsync(B->d_a, B->h_a, n * sizeof(OperandDesc), cudaMemcpyHostToDevice, B->cap);
+            cudaMemcpyAsync(B->d_b, B->h_b, n * sizeof(OperandDesc), cudaMemcpyHostToDevice, B->cap);
+            cudaMemcpyAsync(B->d_out, B->h_out, n * sizeof(OutputDesc), cudaMemcpyHostToDevice,
+                            B->cap);
+            rc = enqueue_chunks(B, B->d_a, B->d_b, B->d_out, B->ws, B->cap, nullptr);
+            cudaError_t e = cudaStreamEndCapture(B->cap, &g);
+            if (rc || e != cudaSuccess || !g) {
+                cudaGetLastError();
+                if (g) cudaGraphDestroy(g);
+                return rc ? rc : GF2X_ECUDA;
+            }
+            e = cudaGraphInstantiate(&B->exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                B->exec = nullptr;
+                return GF2X_ECUDA;
+            }
+        }
+        if (cudaGraphLaunch(B->exec, s) != cudaSuccess || cudaEventRecord(B->done, s) != cudaSuccess) {
+            cudaGetLastError();
+            return GF2X_ECUDA;
+        }
+        B->launched = true;
+        return GF2X_OK;
+    } catch (...) {
+        return GF2X_ECUDA;
+    }
+}
+
+int gf2x_batch_destroy(gf2x_batch *B) {
+    if (!B) return GF2X_EINVAL;
+    if (B->launched) cudaEventSynchronize(B->done);
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->done) cudaEventDestroy(B->done);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    cudaFree(B->ws);
+    cudaFree(B->d_a);
+    cudaFree(B->d_b);
+    cudaFree(B->d_out);
+    cudaFreeHost(B->h_a);
+    cudaFreeHost(B->h_b);
+    cudaFreeHost(B->h_out);
+    cudaGetLastError();
+    delete B;
+    return GF2X_OK;
+}
+
+}  // extern "C"

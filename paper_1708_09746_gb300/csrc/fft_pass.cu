@@ -145,7 +145,10 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool pipe = (a.g64 == nullptr);
     const TileGeom G{c, a.k_lo, g, 4};
-    const uint64_t ntiles = (1ull << a.M) >> (g + c);
+    // tiles of every product: t = (product << tiles_log) | tile
+    const int tiles_log = a.M - g - c;
+    const uint64_t ntiles = (uint64_t)a.count << tiles_log;
+    const uint64_t tmask = (1ull << tiles_log) - 1;
     const uint32_t cmask = (1u << c) - 1;
 
     if (threadIdx.x == 0) {
@@ -159,7 +162,9 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         for (int i = threadIdx.x; i < 4096; i += blockDim.x) dst[i] = __ldg(src + i);
     }
     __syncthreads();
-    if (pipe && warp == 0 && blockIdx.x < ntiles) tile_load_issue(G, a.F, blockIdx.x, buf0, &bar[0], lane);
+    if (pipe && warp == 0 && blockIdx.x < ntiles)
+        tile_load_issue(G, a.F + (blockIdx.x >> tiles_log) * a.strideF, blockIdx.x & tmask, buf0,
+                        &bar[0], lane);
 
     bool aborted = false, prefetched = false;
     uint32_t i = 0;
@@ -167,23 +172,27 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         const int b = i & 1;
         uint4 *s = buf0 + (b ? tile : 0);
         const uint64_t tn = t + gridDim.x;
+        const uint64_t y = t >> tiles_log, tt = t & tmask;  // product, tile
+        uint4 *const Fy = a.F + y * a.strideF;
         bool ok = true;
         prefetched = false;
         if (pipe) {
             if (warp == 0 && tn < ntiles) {
                 bulk_wait_read_all();  // the stores out of buf[b^1] have read it
                 __syncwarp();
-                tile_load_issue(G, a.F, tn, buf0 + (b ? 0 : tile), &bar[b ^ 1], lane);
+                tile_load_issue(G, a.F + (tn >> tiles_log) * a.strideF, tn & tmask,
+                                buf0 + (b ? 0 : tile), &bar[b ^ 1], lane);
                 prefetched = true;
             }
             ok = mbar_wait_bounded(&bar[b], (i >> 1) & 1);
         } else {
             if (warp == 0) bulk_wait_read_all();
             __syncthreads();
-            const uint64_t base = tile_base(G, t);
+            const uint64_t base = tile_base(G, tt);
+            const uint64_t *gy = a.g64 + y * a.strideW;
             for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) {
                 const uint64_t idx = base | ((uint64_t)(q >> c) << a.k_lo) | (q & cmask);
-                s[q] = chrepr_ldg(a.T, __ldg(a.g64 + (idx & a.pmask)));
+                s[q] = chrepr_ldg(a.T, __ldg(gy + (idx & a.pmask)));
             }
         }
         if (!__syncthreads_and(ok)) {
@@ -191,8 +200,8 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
             break;
         }
         // multipliers shared by the tile: cval[r] = s_k(phi(hi << (k_lo + g)))
-        const uint64_t hi = t >> (a.k_lo - c);
-        const uint64_t base = tile_base(G, t);
+        const uint64_t hi = tt >> (a.k_lo - c);
+        const uint64_t base = tile_base(G, tt);
         if ((int)threadIdx.x < g) {
             const int k = a.k_lo + threadIdx.x;
             cval[threadIdx.x] = s_k_of(&a.T->S[k][0], (uint32_t)(hi << (a.k_lo + g)));
@@ -222,7 +231,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         if (a.mode == 2) {  // pointmul with the other operand's transform
             for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) {
                 const uint64_t idx = base | ((uint64_t)(q >> c) << a.k_lo) | (q & cmask);
-                s[q] = mt_gmul128(mt, s[q], __ldg(a.FA + idx));
+                s[q] = mt_gmul128(mt, s[q], __ldg(a.FA + y * a.strideF + idx));
             }
             __syncthreads();
         }
@@ -239,7 +248,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         }
         fence_proxy_async_smem();
         __syncthreads();
-        if (warp == 0) tile_store_issue(G, a.F, t, s, lane);
+        if (warp == 0) tile_store_issue(G, Fy, tt, s, lane);
     }
     if (aborted) {
         if (threadIdx.x == 0) atomicExch(a.status, -4);  // GF2X_ETIMEOUT
@@ -438,7 +447,8 @@ void prepare_fft_attributes() {
 }
 
 int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,
-                    const uint4 *FA, const DevTables *T, int *status, cudaStream_t s) {
+                    const uint4 *FA, const DevTables *T, int *status, cudaStream_t s, int count,
+                    uint64_t strideF, uint64_t strideW) {
     ensure_smem_attr(reinterpret_cast<const void *>(k_fft_pass), 227 * 1024);
     FftPassArgs a;
     a.F = F;
@@ -457,7 +467,10 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
     a.needs_mt = p.needs_mt;
     a.M = M;
     a.status = status;
-    const uint64_t tiles = (1ull << M) >> (p.g + p.c);
+    a.count = count;
+    a.strideF = strideF;
+    a.strideW = strideW;
+    const uint64_t tiles = ((1ull << M) >> (p.g + p.c)) * (uint64_t)count;
     k_fft_pass<<<(unsigned)std::min<uint64_t>(tiles, num_sms()), p.threads, p.smem, s>>>(a);
     return 0;
 }

@@ -35,6 +35,8 @@ struct FftPassArgs {
     bool needs_mt;
     int M;        // log2 of the transform length
     int *status;  // device status word (a bounded wait that ran out stores GF2X_ETIMEOUT)
+    int count;    // products in the launch: product y at F + y * strideF,
+    uint64_t strideF, strideW;  // g64 + y * strideW, FA + y * strideF
 };
 
 // A fixed-capacity list of passes (no heap allocation).
@@ -73,7 +75,8 @@ constexpr int kFftTileLog = 12;
 constexpr int kFftGlobalMax = 8;
 
 int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,
-                    const uint4 *FA, const DevTables *T, int *status, cudaStream_t s);
+                    const uint4 *FA, const DevTables *T, int *status, cudaStream_t s,
+                    int count = 1, uint64_t strideF = 0, uint64_t strideW = 0);
 
 void launch_pointmul_mt(const uint4 *A, const uint4 *B, uint4 *C, uint64_t n, const DevTables *T,
                         cudaStream_t s);

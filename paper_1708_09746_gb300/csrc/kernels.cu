@@ -1,4 +1,7 @@
-// CUDA kernels of the product path (Alg. 5) and their host launchers.
+// CUDA kernels of the product path (Alg. 5) other than the FFT passes, and
+// their host launchers.  Every launcher takes a product count: the products of
+// one batch share a plan and lie in one workspace at a fixed stride, so a
+// batch costs one launch per kernel (blockIdx.y = product).
 #include <algorithm>
 #include <cstdio>
 #include <map>
@@ -15,15 +18,18 @@ namespace gf2x {
 
 // ---------------------------------------------------------------------------
 // Split (Sec. 2.1): copy the operand's words, clear bits past its length and
-// zero-pad to P words.
-__global__ void k_split_pad(const uint64_t *__restrict__ a, uint64_t nw, uint64_t last_mask,
-                            uint64_t *__restrict__ w, uint64_t P) {
+// zero-pad to P words.  Product y reads `many[y]` (or `one` if many is null)
+// and writes w + y * stride.
+__global__ void k_split_pad(OperandDesc one, const OperandDesc *__restrict__ many,
+                            uint64_t *__restrict__ w, uint64_t P, uint64_t stride) {
+    const OperandDesc d = many ? many[blockIdx.y] : one;
+    w += blockIdx.y * stride;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < P;
          i += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t v = 0;
-        if (i < nw) {
-            v = a[i];
-            if (i == nw - 1) v &= last_mask;
+        if (i < d.nw) {
+            v = d.src[i];
+            if (i == d.nw - 1) v &= d.mask;
         }
         w[i] = v;
     }
@@ -60,7 +66,9 @@ __device__ __forceinline__ void bcvt_item(T *f, uint64_t base, uint64_t E, uint6
 }
 
 template <typename T>
-__global__ void k_bcvt_level(T *f, uint64_t n_half, int logE, int loge, int inverse) {
+__global__ void k_bcvt_level(T *f, uint64_t n_half, int logE, int loge, int inverse,
+                             uint64_t stride) {
+    f += blockIdx.y * stride;
     const uint64_t E = 1ull << logE, e = 1ull << loge;
     for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < n_half;
          w += (uint64_t)gridDim.x * blockDim.x) {
@@ -76,9 +84,11 @@ __global__ void k_bcvt_level(T *f, uint64_t n_half, int logE, int loge, int inve
 // (row << c) | col exactly as on the global index, with logE and loge moved
 // by c - lo (the levels in `lb` are given in tile-local form).
 template <typename T>
-__global__ void k_bcvt_tile(T *f, int c, int lo, int w, LevelBatch lb, int inverse) {
+__global__ void k_bcvt_tile(T *f, int c, int lo, int w, LevelBatch lb, int inverse,
+                            uint64_t stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s = reinterpret_cast<T *>(smem_raw);
+    f += blockIdx.y * stride;
     const uint32_t tile = 1u << (c + w);
     const int mid_bits = lo - c;
     const uint64_t mid = blockIdx.x & ((1ull << mid_bits) - 1);
@@ -104,7 +114,8 @@ __global__ void k_bcvt_tile(T *f, int c, int lo, int w, LevelBatch lb, int inver
 // ---------------------------------------------------------------------------
 // changeRepr (Sec. 4.3): F[i] = phi(g[i mod P]), phi by 8-bit tables.  The
 // periodic copy realises the fan-out of the FFT layers whose upper half is
-// zero (Fig. 2).
+// zero (Fig. 2).  (The product path fuses changeRepr into its first FFT pass;
+// this kernel serves the stage entry point.)
 __global__ void k_chrepr(const uint64_t *__restrict__ g, uint64_t pmask, uint4 *__restrict__ F,
                          uint64_t n, const DevTables *__restrict__ T) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
@@ -132,10 +143,12 @@ __device__ __forceinline__ uint4 psi(const DevTables *__restrict__ T, uint4 e) {
     return acc;
 }
 
-__global__ void k_ichrepr_combine(const uint4 *__restrict__ F, uint64_t n, uint64_t *__restrict__ out,
-                                  uint64_t out_words, uint64_t last_mask,
+__global__ void k_ichrepr_combine(const uint4 *__restrict__ F, uint64_t n, uint64_t stride,
+                                  OutputDesc one, const OutputDesc *__restrict__ many,
                                   const DevTables *__restrict__ T) {
-    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < out_words;
+    const OutputDesc d = many ? many[blockIdx.y] : one;
+    F += blockIdx.y * stride;
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < d.words;
          j += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t v = 0;
         if (j < n) {
@@ -146,8 +159,8 @@ __global__ void k_ichrepr_combine(const uint4 *__restrict__ F, uint64_t n, uint6
             uint4 c = psi(T, F[j - 1]);
             v ^= (uint64_t)c.z | ((uint64_t)c.w << 32);
         }
-        if (j == out_words - 1) v &= last_mask;
-        out[j] = v;
+        if (j == d.words - 1) v &= d.mask;
+        d.out[j] = v;
     }
 }
 
@@ -181,15 +194,19 @@ unsigned num_sms() {
     return v;
 }
 
-static inline unsigned grid_for(uint64_t work, unsigned block, unsigned cap = 1u << 20) {
+// Blocks along x for `work` items per product when `count` products share the
+// launch: enough to fill the GPU a few times over, at least one.
+static inline unsigned grid_for(uint64_t work, unsigned block, int count = 1) {
     uint64_t g = (work + block - 1) / block;
-    if (g == 0) g = 1;
-    return (unsigned)std::min<uint64_t>(g, cap);
+    uint64_t cap = std::max<uint64_t>(1, (uint64_t)num_sms() * 16 / (uint64_t)std::max(count, 1));
+    g = std::min(g, std::max<uint64_t>(cap, 1));
+    return (unsigned)std::max<uint64_t>(g, 1);
 }
 
-void launch_split_pad(const uint64_t *a, uint64_t nw, uint64_t last_mask, uint64_t *w, uint64_t P,
-                      cudaStream_t s) {
-    k_split_pad<<<grid_for(P, 256), 256, 0, s>>>(a, nw, last_mask, w, P);
+void launch_split_pad(const OperandDesc &one, const OperandDesc *many, int count, uint64_t *w,
+                      uint64_t P, uint64_t stride, cudaStream_t s) {
+    dim3 grid(grid_for(P, 256, count), count);
+    k_split_pad<<<grid, 256, 0, s>>>(one, many, w, P, stride);
 }
 
 // Tiles of 128 KiB: 2^14 words or 2^13 128-bit elements; rows of at least
@@ -207,7 +224,8 @@ static int min_cols_for() {
 // tile together (with >= min_cols low column bits, or contiguous) share one
 // pass; a level too wide for any tile is a streaming pass of its own.
 template <typename T>
-uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStream_t s) {
+uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStream_t s, int count,
+                       uint64_t stride) {
     ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<T>),
                      (int)(sizeof(T) << tile_log_for<T>()));
     uint64_t launches = 0;
@@ -219,18 +237,19 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
         if (ghi + 1 <= budget) return true;
         return glo >= cmin && (ghi - glo + 1) + cmin <= budget;
     };
-    size_t i = 0;
-    while (i < (size_t)lv.n) {
+    int i = 0;
+    while (i < lv.n) {
         int glo = lv.v[i].loge, ghi = lv.v[i].logE;
         if (!fits(glo, ghi)) {
-            k_bcvt_level<T><<<grid_for(n / 2, 256), 256, 0, s>>>(f, n / 2, lv.v[i].logE, lv.v[i].loge,
-                                                                 inverse);
+            dim3 grid(grid_for(n / 2, 256, count), count);
+            k_bcvt_level<T><<<grid, 256, 0, s>>>(f, n / 2, lv.v[i].logE, lv.v[i].loge, inverse,
+                                                 stride);
             launches++;
             i++;
             continue;
         }
-        size_t j = i + 1;
-        while (j < (size_t)lv.n && (int)(j - i) < LevelBatch::kMax &&
+        int j = i + 1;
+        while (j < lv.n && j - i < LevelBatch::kMax &&
                fits(std::min(glo, (int)lv.v[j].loge), std::max(ghi, (int)lv.v[j].logE))) {
             glo = std::min(glo, (int)lv.v[j].loge);
             ghi = std::max(ghi, (int)lv.v[j].logE);
@@ -248,14 +267,15 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
         }
         LevelBatch lb{};
         lb.count = 0;
-        for (size_t q = i; q < j; q++) {
+        for (int q = i; q < j; q++) {
             lb.logE[lb.count] = (int8_t)(lv.v[q].logE - lo + c);
             lb.loge[lb.count] = (int8_t)(lv.v[q].loge - lo + c);
             lb.count++;
         }
         size_t smem = sizeof(T) << (c + w);
         int threads = std::max(32, std::min(512, 1 << (c + w - 1)));
-        k_bcvt_tile<T><<<(unsigned)(n >> (c + w)), threads, smem, s>>>(f, c, lo, w, lb, inverse);
+        dim3 grid((unsigned)(n >> (c + w)), count);
+        k_bcvt_tile<T><<<grid, threads, smem, s>>>(f, c, lo, w, lb, inverse, stride);
         launches++;
         i = j;
     }
@@ -270,17 +290,21 @@ void prepare_bcvt_attributes() {
     num_sms();
 }
 
-template uint64_t run_basis_cvt<uint64_t>(uint64_t *, int, const LevelList &, int, cudaStream_t);
-template uint64_t run_basis_cvt<uint4>(uint4 *, int, const LevelList &, int, cudaStream_t);
+template uint64_t run_basis_cvt<uint64_t>(uint64_t *, int, const LevelList &, int, cudaStream_t,
+                                          int, uint64_t);
+template uint64_t run_basis_cvt<uint4>(uint4 *, int, const LevelList &, int, cudaStream_t, int,
+                                       uint64_t);
 
 void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const DevTables *T,
                    cudaStream_t s) {
     k_chrepr<<<grid_for(n, 256), 256, 0, s>>>(g, P - 1, F, n, T);
 }
 
-void launch_ichrepr_combine(const uint4 *F, uint64_t n, uint64_t *out, uint64_t out_words,
-                            uint64_t last_mask, const DevTables *T, cudaStream_t s) {
-    k_ichrepr_combine<<<grid_for(out_words, 256), 256, 0, s>>>(F, n, out, out_words, last_mask, T);
+void launch_ichrepr_combine(const uint4 *F, uint64_t n, uint64_t stride, const OutputDesc &one,
+                            const OutputDesc *many, int count, uint64_t max_words,
+                            const DevTables *T, cudaStream_t s) {
+    dim3 grid(grid_for(max_words, 256, count), count);
+    k_ichrepr_combine<<<grid, 256, 0, s>>>(F, n, stride, one, many, T);
 }
 
 }  // namespace gf2x

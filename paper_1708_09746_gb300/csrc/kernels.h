@@ -3,7 +3,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <vector>
 
 #include "gf2x_internal.h"
 
@@ -19,6 +18,20 @@ struct LevelBatch {
     int8_t loge[kMax];
 };
 
+// One operand of a product as Split reads it: nw words, the last one masked.
+struct OperandDesc {
+    const uint64_t *src;
+    uint64_t nw;
+    uint64_t mask;
+};
+
+// The output of a product as InterleavedCombine writes it.
+struct OutputDesc {
+    uint64_t *out;
+    uint64_t words;
+    uint64_t mask;
+};
+
 // Raises the dynamic shared-memory limit of `func` to `bytes` once per device
 // (the attribute is per device context).
 void ensure_smem_attr(const void *func, int bytes);
@@ -32,19 +45,26 @@ unsigned num_sms();
 void prepare_bcvt_attributes();
 void prepare_fft_attributes();
 
-void launch_split_pad(const uint64_t *a, uint64_t nw, uint64_t last_mask, uint64_t *w, uint64_t P,
-                      cudaStream_t s);
+// Split of `count` operands: product y reads many[y] (or `one` when many is
+// null) and writes P words at w + y * stride.
+void launch_split_pad(const OperandDesc &one, const OperandDesc *many, int count, uint64_t *w,
+                      uint64_t P, uint64_t stride, cudaStream_t s);
 
 // BasisCvt (inverse = 0) or iBasisCvt (inverse = 1) on 2^m coefficients of
-// type T (uint64_t or uint4), with the forward level list `fwd`.  The run_*
-// launchers return the number of kernel launches they enqueued.
+// type T (uint64_t or uint4), with the forward level list `fwd`, for `count`
+// arrays at f + y * stride.  Returns the number of kernel launches enqueued.
 template <typename T>
-uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStream_t s);
+uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStream_t s,
+                       int count = 1, uint64_t stride = 0);
 
 void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const DevTables *T,
                    cudaStream_t s);
 
-void launch_ichrepr_combine(const uint4 *F, uint64_t n, uint64_t *out, uint64_t out_words,
-                            uint64_t last_mask, const DevTables *T, cudaStream_t s);
+// changeRepr^-1 + InterleavedCombine of `count` products: product y reads n
+// elements at F + y * stride and writes many[y] (or `one`); max_words bounds
+// the output lengths.
+void launch_ichrepr_combine(const uint4 *F, uint64_t n, uint64_t stride, const OutputDesc &one,
+                            const OutputDesc *many, int count, uint64_t max_words,
+                            const DevTables *T, cudaStream_t s);
 
 }  // namespace gf2x

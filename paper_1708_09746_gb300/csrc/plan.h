@@ -10,6 +10,7 @@
 #include "fft_pass.h"
 #include "gf2x_dev.cuh"
 #include "gf2x_internal.h"
+#include "kernels.h"
 
 struct gf2x_plan {
     uint64_t na_bits, nb_bits, na_w, nb_w, out_words, total_bits;
@@ -56,6 +57,18 @@ int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits, PassTableFn src)
 // 256-byte aligned), tables T and status word `status`; `hook` may be null.
 int plan_run_core(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out,
                   void *ws, cudaStream_t s, const DevTables *T, int *status, StageHook *hook);
+
+// `count` products sharing plan p (same M, log2 Pa, log2 Pb): product y's
+// operands and output from many_a[y], many_b[y], many_out[y] (device arrays;
+// null = the single `one_*`), its workspace at ws + y * ws_stride;
+// max_out_words bounds the outputs' lengths.
+int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
+                   const OperandDesc *many_b, const OutputDesc *many_out, const OperandDesc &one_a,
+                   const OperandDesc &one_b, const OutputDesc &one_out, uint64_t max_out_words,
+                   void *ws, size_t ws_stride, cudaStream_t s, const DevTables *T, int *status,
+                   StageHook *hook);
+
+uint64_t mask_of_bits(uint64_t bits);
 
 // Host image of the size-independent device tables.
 void fill_dev_tables(DevTables *h);
