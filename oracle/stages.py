@@ -355,6 +355,40 @@ def eval_novelpoly(g, x):
     return acc
 
 
+def _split128(vals):
+    lo = np.array([v & (2**64 - 1) for v in vals], dtype=np.uint64)
+    hi = np.array([v >> 64 for v in vals], dtype=np.uint64)
+    return lo, hi
+
+
+def novel_basis_at(n, x):
+    """X_j(x) for j < n (n a power of two), as (lo, hi) uint64 arrays.
+    Def. 2.3 written out over the bits of j: the values for j < 2^(i+1) are
+    those for j < 2^i followed by the same values times s_i(x)."""
+    lo = np.zeros(n, dtype=np.uint64)
+    hi = np.zeros(n, dtype=np.uint64)
+    lo[0] = np.uint64(1)
+    size, i = 1, 0
+    while size < n:
+        si = s_k(i, x)
+        slo = np.full(size, np.uint64(si & (2**64 - 1)))
+        shi = np.full(size, np.uint64(si >> 64))
+        lo[size:2 * size], hi[size:2 * size] = tmul_vec(lo[:size], hi[:size], slo, shi)
+        size *= 2
+        i += 1
+    return lo, hi
+
+
+def eval_novelpoly_np(g_lo, g_hi, x):
+    """f(x) = sum_j g_j X_j(x) for coefficients given as (lo, hi) uint64
+    arrays of power-of-two length: the same sum as eval_novelpoly, with the
+    n products taken by one vectorised tower multiplication."""
+    n = len(g_lo)
+    Xl, Xh = novel_basis_at(n, x)
+    pl, ph = tmul_vec(g_lo, g_hi, Xl, Xh)
+    return int(np.bitwise_xor.reduce(pl)) | (int(np.bitwise_xor.reduce(ph)) << 64)
+
+
 # ---------------------------------------------------------------------------
 # changeRepr (Sec. 4.3): 64-bit block p(z) -> p(r) with r = x_7 = v_64.
 

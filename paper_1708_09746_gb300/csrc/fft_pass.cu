@@ -362,6 +362,9 @@ size_t pass_smem(int g, int c, int uf, bool needs_mt) {
 }
 
 int make_pass(int k_lo, int g, int c, int uf, int mode, int g_f, PassTableFn src, FftPassCfg *p) {
+    // register sub-passes need a warp's 32 lanes inside the column bits and
+    // the rows below the sub-pass, so that the lanes share the multiplier
+    if (uf < g && c + uf < 5) return -1;
     int rc = (src ? src : cached_pass_tables)(k_lo, g, uf, &p->d_val, &p->d_shfl);
     if (rc) return rc;
     p->k_lo = k_lo;

@@ -72,7 +72,7 @@ int plan_fft_fused(int M, int log_p, PassList &fwd_global, FftPassCfg &local, Pa
 
 // Layers of the contiguous bottom pass and of each strided pass.
 constexpr int kFftTileLog = 12;
-constexpr int kFftGlobalMax = 8;
+constexpr int kFftGlobalMax = 7;  // keeps c = 12 - g >= 5 (warp-uniform multipliers)
 
 int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,
                     const uint4 *FA, const DevTables *T, int *status, cudaStream_t s,

@@ -150,6 +150,21 @@ def test_fft_vs_direct_evaluation(n, alpha):
     assert S.ifft_lch(F, alpha) == g
 
 
+def test_vectorised_novelpoly_evaluation():
+    # the vectorised sum agrees with the term-by-term one, and X_j vanishes
+    # on V_b whenever bit b of j is set (s_b has the roots V_b)
+    g = _rand128(32)
+    glo, ghi = S._split128(g)
+    for x in [0, 1, 5, 31, 0x1234, (1 << 70) + 3]:
+        assert S.eval_novelpoly_np(glo, ghi, x) == S.eval_novelpoly(g, x)
+    lo, hi = S.novel_basis_at(64, 5)
+    assert all(int(lo[j]) == 0 and int(hi[j]) == 0 for j in range(8, 64))
+    assert any(int(lo[j]) or int(hi[j]) for j in range(8))
+    lo, hi = S.novel_basis_at(8, 0x99)
+    for i in range(3):
+        assert int(lo[1 << i]) | (int(hi[1 << i]) << 64) == S.s_k(i, 0x99)
+
+
 def test_chrepr_homomorphism_and_inverse():
     xs = [int(x) for x in W.random_words(77, 8)]
     for p in xs[:4]:
