@@ -112,6 +112,114 @@ __global__ void k_bcvt_tile(T *f, int c, int lo, int w, LevelBatch lb, int inver
 }
 
 // ---------------------------------------------------------------------------
+// The top VarSubs of a BasisCvt of 2^m coefficients, m = 16 + h with
+// 1 <= h <= 8 (Alg. 3 with K = 16): the h divisions by x^E + x^e with
+// E = 2^(16+j), e = 2^j, j = h-1 .. 0.  These are the only levels whose
+// mixing range (17 index bits) is too wide for a shared-memory tile.
+//
+// Every XOR of division j joins two indices that differ by E - e = 2^j D,
+// D = 2^16 - 1, so the array splits into independent classes
+// {c + n D : n >= 0}, c < D, whose members we call rows n.  As
+// c + n D = n 2^16 + (c - n), for a class with c >= 3 * 2^(h-1) (so that
+// c - n >= 2^(h-1) >= e for every row n < 2^h) the position of row n inside
+// its segment of 2E coefficients is (n mod 2^(j+1)) 2^16 + (c - n): step 1
+// never applies and step 2 applies exactly to the rows with bit j of n clear,
+// row[n] ^= row[n + 2^j].  On such a class the h divisions are therefore the
+// transform row[n] = XOR of row[n'] over n' containing the bits of n, which
+// is its own inverse and does not depend on the order of the levels.  A
+// thread holds one 32-bit limb of 2^HR rows of a class in registers (the
+// divisions act bitwise, so limbs are independent); the remaining h - HR row
+// bits are spread over lanes and joined by shuffles.  The classes
+// c < 3 * 2^(h-1) (at most 384, where a row may sit at the start of its
+// segment) take the two steps of every division exactly, in shared memory.
+
+constexpr uint32_t kTopD = 65535;         // 2^16 - 1
+constexpr int kTopThreads = 128;
+constexpr uint32_t kTopBoundaryClasses = 8;  // classes per boundary CTA
+
+__host__ __device__ constexpr uint32_t top_boundary(int h) { return (1u << h) + (1u << (h - 1)); }
+
+template <typename T, int HR>
+__global__ void __launch_bounds__(kTopThreads) k_bcvt_top(T *f, int h, int inverse,
+                                                          uint32_t n_bnd_ctas, uint64_t stride) {
+    f += blockIdx.y * stride;
+    const uint32_t B = top_boundary(h);
+    if (blockIdx.x < n_bnd_ctas) {
+        // boundary classes [c0, c0 + 8) intersected with [0, B)
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        T *s = reinterpret_cast<T *>(smem_raw);
+        const uint64_t n_el = 1ull << (16 + h);
+        const uint32_t R = (1u << h) + 1, items = kTopBoundaryClasses * R;
+        const uint32_t c0 = blockIdx.x * kTopBoundaryClasses;
+        for (uint32_t q = threadIdx.x; q < items; q += blockDim.x) {
+            const uint32_t c = c0 + q / R;
+            const uint64_t x = c + (uint64_t)(q % R) * kTopD;
+            T v;
+            memset(&v, 0, sizeof(T));
+            if (c < B && x < n_el) v = f[x];
+            s[q] = v;
+        }
+        __syncthreads();
+        for (int it = 0; it < h; it++) {
+            const int j = inverse ? it : h - 1 - it;
+            const uint64_t E = 1ull << (16 + j), e = 1ull << j;
+            for (int st = 0; st < 2; st++) {
+                // forward: step 1 then step 2; inverse: step 2 then step 1
+                const bool step1 = (st == 0) != (inverse != 0);
+                for (uint32_t q = threadIdx.x; q < items; q += blockDim.x) {
+                    const uint32_t c = c0 + q / R, n = q % R;
+                    if (c >= B || n + (1u << j) >= R) continue;
+                    const uint64_t x = c + (uint64_t)n * kTopD;
+                    if (x + ((uint64_t)kTopD << j) >= n_el) continue;
+                    const uint64_t o = x & (2 * E - 1);
+                    const bool act = step1 ? (o >= E && o < E + e) : (o >= e && o < E);
+                    if (act) s[q] = xr(s[q], s[q + (1u << j)]);
+                }
+                __syncthreads();
+            }
+        }
+        for (uint32_t q = threadIdx.x; q < items; q += blockDim.x) {
+            const uint32_t c = c0 + q / R;
+            const uint64_t x = c + (uint64_t)(q % R) * kTopD;
+            if (c < B && x < n_el) f[x] = s[q];
+        }
+        return;
+    }
+    // interior classes
+    constexpr int L = sizeof(T) / 4;
+    const int LB = h - HR;      // row bits held across lanes (0 .. 2)
+    const int G = 32 >> LB;     // lanes per row group
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cl = lane & (G - 1), nh = lane >> (5 - LB);
+    const uint32_t cls_per_warp = G / L;
+    const uint32_t c = B + (blockIdx.x - n_bnd_ctas) * (cls_per_warp * (kTopThreads / 32)) +
+                       warp * cls_per_warp + cl / L;
+    const bool valid = c < kTopD;
+    uint32_t *F = reinterpret_cast<uint32_t *>(f) + (uint64_t)c * L + (cl % L);
+    const uint64_t rowstep = (uint64_t)kTopD * L;
+    uint32_t v[1 << HR];
+#pragma unroll
+    for (int i = 0; i < (1 << HR); i++)
+        v[i] = valid ? F[(((uint64_t)nh << HR) | i) * rowstep] : 0u;
+#pragma unroll
+    for (int j = 0; j < HR; j++)
+#pragma unroll
+        for (int i = 0; i < (1 << HR); i++)
+            if (!((i >> j) & 1)) v[i] ^= v[i + (1 << j)];
+    for (int b = 0; b < LB; b++) {
+#pragma unroll
+        for (int i = 0; i < (1 << HR); i++) {
+            const uint32_t p = __shfl_xor_sync(0xffffffffu, v[i], G << b);
+            if (!((nh >> b) & 1)) v[i] ^= p;
+        }
+    }
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < (1 << HR); i++) F[(((uint64_t)nh << HR) | i) * rowstep] = v[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // changeRepr (Sec. 4.3): F[i] = phi(g[i mod P]), phi by 8-bit tables.  The
 // periodic copy realises the fan-out of the FFT layers whose upper half is
 // zero (Fig. 2).  (The product path fuses changeRepr into its first FFT pass;
@@ -220,17 +328,56 @@ static int min_cols_for() {
     return sizeof(T) == 8 ? 4 : 3;
 }
 
+// Number of leading forward levels that form the top VarSubs with K = 16
+// (k_bcvt_top), 0 when the size has none or it is handled level by level.
+static int top_levels(int m, const LevelList &fwd) {
+    if (m < 17 || m > 24) return 0;
+    const int h = m - 16;
+    if (fwd.n < h) return 0;
+    for (int q = 0; q < h; q++)
+        if (fwd.v[q].logE != m - 1 - q || fwd.v[q].loge != h - 1 - q) return 0;
+    return h;
+}
+
+template <typename T>
+static void launch_bcvt_top(T *f, int h, int inverse, cudaStream_t s, int count, uint64_t stride) {
+    constexpr int L = sizeof(T) / 4;
+    const int HR = std::min(h, 6), LB = h - HR;
+    const uint32_t B = top_boundary(h);
+    const uint32_t nb = (B + kTopBoundaryClasses - 1) / kTopBoundaryClasses;
+    const uint32_t per_cta = (uint32_t)(kTopThreads / 32) * (uint32_t)((32 >> LB) / L);
+    const uint32_t ni = (kTopD - B + per_cta - 1) / per_cta;
+    const dim3 grid(nb + ni, count);
+    const size_t smem = (size_t)kTopBoundaryClasses * ((1u << h) + 1) * sizeof(T);
+    switch (HR) {
+        case 1: k_bcvt_top<T, 1><<<grid, kTopThreads, smem, s>>>(f, h, inverse, nb, stride); break;
+        case 2: k_bcvt_top<T, 2><<<grid, kTopThreads, smem, s>>>(f, h, inverse, nb, stride); break;
+        case 3: k_bcvt_top<T, 3><<<grid, kTopThreads, smem, s>>>(f, h, inverse, nb, stride); break;
+        case 4: k_bcvt_top<T, 4><<<grid, kTopThreads, smem, s>>>(f, h, inverse, nb, stride); break;
+        case 5: k_bcvt_top<T, 5><<<grid, kTopThreads, smem, s>>>(f, h, inverse, nb, stride); break;
+        default: k_bcvt_top<T, 6><<<grid, kTopThreads, smem, s>>>(f, h, inverse, nb, stride); break;
+    }
+}
+
 // Greedy schedule: consecutive levels whose mixing ranges [loge, logE] fit one
 // tile together (with >= min_cols low column bits, or contiguous) share one
-// pass; a level too wide for any tile is a streaming pass of its own.
+// pass; a level too wide for any tile is a streaming pass of its own.  The
+// top VarSubs of sizes 2^17 .. 2^24 is one k_bcvt_top pass (first in the
+// forward direction, last in the inverse).
 template <typename T>
 uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStream_t s, int count,
                        uint64_t stride) {
     ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<T>),
                      (int)(sizeof(T) << tile_log_for<T>()));
     uint64_t launches = 0;
+    const int h_top = top_levels(m, fwd);
     LevelList lv;
-    for (int q = 0; q < fwd.n; q++) lv.push(fwd.v[inverse ? fwd.n - 1 - q : q]);
+    for (int q = 0; q < fwd.n - h_top; q++)
+        lv.push(fwd.v[inverse ? fwd.n - 1 - q : h_top + q]);
+    if (h_top && !inverse) {
+        launch_bcvt_top<T>(f, h_top, 0, s, count, stride);
+        launches++;
+    }
     const int budget = std::min(tile_log_for<T>(), m), cmin = min_cols_for<T>();
     const uint64_t n = 1ull << m;
     auto fits = [&](int glo, int ghi) {
@@ -278,6 +425,10 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
         k_bcvt_tile<T><<<grid, threads, smem, s>>>(f, c, lo, w, lb, inverse, stride);
         launches++;
         i = j;
+    }
+    if (h_top && inverse) {
+        launch_bcvt_top<T>(f, h_top, 1, s, count, stride);
+        launches++;
     }
     return launches;
 }
