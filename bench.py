@@ -148,7 +148,7 @@ def _peaks():
         return {}
 
 
-def cpu_sample(a, na, b, nb, depth, reps=1):
+def cpu_sample(a, na, b, nb, depth, reps=1, single_thread=False):
     """Time the oracle on one depth-`depth` Karatsuba sub-product of the
     workload (the product of the lowest 2^-depth parts of a and b) on all
     host cores and scale by 3^depth to ms per full product.  The linear
@@ -164,12 +164,38 @@ def cpu_sample(a, na, b, nb, depth, reps=1):
         dt = time.perf_counter() - t0
         best = dt if best is None else min(best, dt)
     scale = 3 ** depth
-    return {"value": best * 1e3 * scale, "unit": "ms", "cores": P.num_threads(),
-            "kind": "oracle",
-            "sample": "1 of 3^%d Karatsuba sub-products (%d x %d bits: the low "
-                      "parts of a and b), all cores, x%d; upper-level linear "
-                      "recombination not included" % (depth, 64 * sub_w, 64 * sub_w, scale),
-            "sample_s": best}
+    out = {"value": best * 1e3 * scale, "unit": "ms", "cores": P.num_threads(),
+           "kind": "oracle",
+           "sample": "1 of 3^%d Karatsuba sub-products (%d x %d bits: the low "
+                     "parts of a and b), all cores, x%d; upper-level linear "
+                     "recombination not included" % (depth, 64 * sub_w, 64 * sub_w, scale),
+           "sample_s": best}
+    if single_thread:
+        # the same estimate on one core, from a sub-product two levels deeper
+        d1 = depth + 2
+        w1 = max(1, nw >> d1)
+        t0 = time.perf_counter()
+        P.mul(a[:w1].copy(), 64 * w1, b[:w1].copy(), 64 * w1, threads=1)
+        dt1 = time.perf_counter() - t0
+        out["one_core"] = {"value": dt1 * 1e3 * 3 ** d1, "unit": "ms", "cores": 1,
+                           "sample": "1 of 3^%d sub-products (%d x %d bits), one core, x%d"
+                                     % (d1, 64 * w1, 64 * w1, 3 ** d1),
+                           "sample_s": dt1}
+    out["host"] = _host_cpu()
+    return out
+
+
+def _host_cpu():
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    import platform
+    return {"machine": platform.machine(), "model": model, "nproc": os.cpu_count()}
 
 
 def run_reference(args):
@@ -466,7 +492,7 @@ def run_ours(args):
         except Exception as e:
             line["serving"] = {"error": repr(e)}
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_sample(a, na, b, nb, args.cpu_depth)
+        line["cpu_baseline"] = cpu_sample(a, na, b, nb, args.cpu_depth, single_thread=True)
     print(json.dumps(line))
 
 

@@ -127,33 +127,76 @@ __device__ __forceinline__ uint4 chrepr_ldg(const DevTables *__restrict__ T, uin
     return acc;
 }
 
+// Multiplier s_k(phi(hi << (k_lo + g))) shared by a tile of layer k = k_lo + r
+// (hi = the tile index bits above the tile).
+__device__ __forceinline__ uint32_t tile_cval(const FftPassArgs &a, uint64_t tt, int r) {
+    const uint64_t hi = tt >> (a.k_lo - a.c);
+    return s_k_of(&a.T->S[a.k_lo + r][0], (uint32_t)(hi << (a.k_lo + a.g)));
+}
+
+// Starts the asynchronous copies of the byte-sliced shuffle tables of the
+// multipliers cv[r], r = uf .. g-1 (Sec. 4.4: the table of c is the XOR of
+// the tables of its four bytes) into stab[(r - uf) * 4 + byte][224].
+__device__ __forceinline__ void prefetch_tables(const FftPassArgs &a, const uint32_t *cv,
+                                                uint32_t *stab) {
+    const int gt = a.g - a.uf;
+    for (int q = threadIdx.x; q < gt * 4 * 56; q += blockDim.x) {
+        const int piece = q / 56, chunk = q - piece * 56;
+        const int r = a.uf + (piece >> 2), p = piece & 3;
+        const uint32_t byte = (cv[r] >> (8 * p)) & 255;
+        cp_async16(stab + piece * 224 + chunk * 4, &a.T->shfl_m4r[p][byte][0][0] + chunk * 4);
+    }
+    cp_async_commit();
+}
+
 // Persistent kernel: each CTA walks the tiles blockIdx.x, +gridDim.x, ...
 // with two tile buffers.  While one tile is computed, the next one is being
 // loaded by bulk copies (TMA) and the previous one stored; warp 0 issues all
-// copies.  A pass whose input is the 64-bit block array (changeRepr fused into
-// the first pass) loads with ordinary loads instead.
+// copies.  The first pass of a transform reads the 64-bit blocks instead and
+// applies changeRepr on the way in; when the pass has room (no product table)
+// those blocks are also staged ahead by bulk copies, otherwise they are read
+// with ordinary loads.  The shuffle tables of the next tile's multipliers
+// are copied in asynchronously while the current tile is computed.
 __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int g = a.g, c = a.c, uf = a.uf;
+    const int g = a.g, c = a.c, uf = a.uf, gt = g - uf;
     const uint32_t tile = 1u << (g + c);
     uint4 *const buf0 = reinterpret_cast<uint4 *>(smem);  // buffer b at buf0 + b * tile
-    uint32_t *ctab = reinterpret_cast<uint32_t *>(smem + 32 * (size_t)tile);  // [g-uf][7][32]
-    uint32_t *cval = ctab + (g - uf) * 224;                                   // [32]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(cval + 32);                 // [2]
-    uint8_t *mt = reinterpret_cast<uint8_t *>(bar + 2);                      // 64 KiB if needed
+    uint32_t *ctab = reinterpret_cast<uint32_t *>(smem + 32 * (size_t)tile);  // [gt][7][32]
+    uint32_t *stab = ctab + gt * 224;                                         // [gt][4][224]
+    uint32_t *cval = stab + gt * 4 * 224;                                     // [32]
+    uint32_t *cnext = cval + 32;                                              // [32]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(cnext + 32);                 // [4]
+    unsigned char *tail = reinterpret_cast<unsigned char *>(bar + 4);
+    const bool from_g = a.g64 != nullptr;
+    const bool pipe = !from_g;                // tiles of F by bulk copies
+    // 64-bit blocks staged by bulk copies: needs room (no product table) and
+    // rows of at least 16 bytes (c >= 1; strided passes have c >= 5)
+    const bool gpipe = from_g && !a.needs_mt && c >= 1;
+    uint64_t *g64s = reinterpret_cast<uint64_t *>(tail);             // [tile] if gpipe
+    uint8_t *mt = tail + (gpipe ? 8 * (size_t)tile : 0);             // 64 KiB if needed
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool pipe = (a.g64 == nullptr);
     const TileGeom G{c, a.k_lo, g, 4};
+    const TileGeom G8{c, a.k_lo, g, 3};
     // tiles of every product: t = (product << tiles_log) | tile
     const int tiles_log = a.M - g - c;
     const uint64_t ntiles = (uint64_t)a.count << tiles_log;
     const uint64_t tmask = (1ull << tiles_log) - 1;
     const uint32_t cmask = (1u << c) - 1;
+    // The 64-bit blocks of tile t: rows of the same shape at the index taken
+    // modulo P.  The pass's layers lie below log2 P, so only the tile's high
+    // bits are reduced: the block tile number keeps the middle bits and the
+    // high bits modulo P >> (k_lo + g).
+    const int mid_bits = a.k_lo - c;
+    auto g_tile_src = [&](uint64_t t) { return a.g64 + (t >> tiles_log) * a.strideW; };
+    auto g_tile_of = [&](uint64_t tt) {
+        return (((tt >> mid_bits) & (a.pmask >> (a.k_lo + g))) << mid_bits) |
+               (tt & ((1ull << mid_bits) - 1));
+    };
 
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int i = 0; i < 3; i++) mbar_init(&bar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (a.needs_mt) {
@@ -161,10 +204,18 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         uint4 *dst = reinterpret_cast<uint4 *>(mt);
         for (int i = threadIdx.x; i < 4096; i += blockDim.x) dst[i] = __ldg(src + i);
     }
+    if ((int)threadIdx.x < g && blockIdx.x < ntiles)
+        cnext[threadIdx.x] = tile_cval(a, blockIdx.x & tmask, threadIdx.x);
     __syncthreads();
-    if (pipe && warp == 0 && blockIdx.x < ntiles)
-        tile_load_issue(G, a.F + (blockIdx.x >> tiles_log) * a.strideF, blockIdx.x & tmask, buf0,
-                        &bar[0], lane);
+    if (blockIdx.x < ntiles) {
+        prefetch_tables(a, cnext, stab);
+        if (warp == 0 && pipe)
+            tile_load_issue(G, a.F + (blockIdx.x >> tiles_log) * a.strideF, blockIdx.x & tmask,
+                            buf0, &bar[0], lane);
+        if (warp == 0 && gpipe)
+            tile_load_issue(G8, g_tile_src(blockIdx.x), g_tile_of(blockIdx.x & tmask), g64s, &bar[2],
+                            lane);
+    }
 
     bool aborted = false, prefetched = false;
     uint32_t i = 0;
@@ -186,36 +237,39 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
             }
             ok = mbar_wait_bounded(&bar[b], (i >> 1) & 1);
         } else {
-            if (warp == 0) bulk_wait_read_all();
-            __syncthreads();
-            const uint64_t base = tile_base(G, tt);
+            if (warp == 0) bulk_wait_read_all();  // the stores out of buf[b] have read it
+            if (gpipe) ok = mbar_wait_bounded(&bar[2], i & 1);
+        }
+        cp_async_wait_all();
+        if (!__syncthreads_and(ok)) {
+            aborted = true;
+            break;
+        }
+        // this tile's shuffle tables and multipliers
+        for (int q = threadIdx.x; q < gt * 224; q += blockDim.x) {
+            const uint32_t *p4 = stab + (q / 224) * 896 + (q % 224);
+            ctab[q] = p4[0] ^ p4[224] ^ p4[448] ^ p4[672];
+        }
+        if (threadIdx.x < 32) cval[threadIdx.x] = cnext[threadIdx.x];
+        const uint64_t base = tile_base(G, tt);
+        if (gpipe) {
+            for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) s[q] = chrepr_ldg(a.T, g64s[q]);
+        } else if (from_g) {
             const uint64_t *gy = a.g64 + y * a.strideW;
             for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) {
                 const uint64_t idx = base | ((uint64_t)(q >> c) << a.k_lo) | (q & cmask);
                 s[q] = chrepr_ldg(a.T, __ldg(gy + (idx & a.pmask)));
             }
         }
-        if (!__syncthreads_and(ok)) {
-            aborted = true;
-            break;
-        }
-        // multipliers shared by the tile: cval[r] = s_k(phi(hi << (k_lo + g)))
-        const uint64_t hi = tt >> (a.k_lo - c);
-        const uint64_t base = tile_base(G, tt);
-        if ((int)threadIdx.x < g) {
-            const int k = a.k_lo + threadIdx.x;
-            cval[threadIdx.x] = s_k_of(&a.T->S[k][0], (uint32_t)(hi << (a.k_lo + g)));
-        }
         __syncthreads();
-        for (int q = threadIdx.x; q < (g - uf) * 224; q += blockDim.x) {
-            const int r = uf + q / 224, wl = q % 224;
-            const uint32_t cv = cval[r];
-            const uint32_t *tb = &a.T->shfl_m4r[0][0][0][0] + wl;
-            ctab[q] = __ldg(tb + (cv & 255) * 224) ^ __ldg(tb + (256 + ((cv >> 8) & 255)) * 224) ^
-                      __ldg(tb + (512 + ((cv >> 16) & 255)) * 224) ^
-                      __ldg(tb + (768 + (cv >> 24)) * 224);
+        // prefetch the next tile's blocks and multipliers' tables
+        if (gpipe && warp == 0 && tn < ntiles) {
+            tile_load_issue(G8, g_tile_src(tn), g_tile_of(tn & tmask), g64s, &bar[2], lane);
+            prefetched = true;
         }
+        if ((int)threadIdx.x < g && tn < ntiles) cnext[threadIdx.x] = tile_cval(a, tn & tmask, threadIdx.x);
         __syncthreads();
+        if (tn < ntiles) prefetch_tables(a, cnext, stab);
 
         if (a.mode != 1) {  // forward layers g_f-1 .. 0
             for (int r_hi = a.g_f - 1; r_hi >= uf; r_hi -= 3) {
@@ -253,8 +307,14 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     if (aborted) {
         if (threadIdx.x == 0) atomicExch(a.status, -4);  // GF2X_ETIMEOUT
         // let a prefetch already in flight land before the CTA exits
-        if (prefetched && threadIdx.x == 0) mbar_wait_bounded(&bar[(i & 1) ^ 1], ((i + 1) >> 1) & 1);
+        if (prefetched && threadIdx.x == 0) {
+            if (pipe)
+                mbar_wait_bounded(&bar[(i & 1) ^ 1], ((i + 1) >> 1) & 1);
+            else
+                mbar_wait_bounded(&bar[2], (i + 1) & 1);
+        }
     }
+    cp_async_wait_all();
     if (warp == 0) bulk_wait_all();
 }
 
@@ -263,7 +323,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
 __global__ void __launch_bounds__(256) k_pointmul_mt(const uint4 *__restrict__ A, const uint4 *B,
                                                       uint4 *C, uint64_t n,
                                                       const DevTables *__restrict__ T) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     uint8_t *mt = smem;
     const uint4 *src = reinterpret_cast<const uint4 *>(T->mul8);
     for (int i = threadIdx.x; i < 4096; i += blockDim.x) reinterpret_cast<uint4 *>(mt)[i] = __ldg(src + i);
@@ -354,9 +414,14 @@ int cached_pass_tables(int k_lo, int g, int uf, const uint32_t **d_val, const ui
     return 0;
 }
 
-size_t pass_smem(int g, int c, int uf, bool needs_mt) {
-    size_t b = (size_t)32 << (g + c);  // two tile buffers
-    b += (size_t)(g - uf) * 224 * 4 + 32 * 4 + 16;
+// Shared memory of a pass: two tile buffers, the shuffle tables of the tile's
+// multipliers and their staged byte slices, the multipliers, four mbarriers,
+// then the staged 64-bit blocks (first pass without product table) and the
+// F~_{2^8} product table if needed.
+size_t pass_smem(int g, int c, int uf, bool needs_mt, bool from_g) {
+    size_t b = (size_t)32 << (g + c);
+    b += (size_t)(g - uf) * 224 * 4 * 5 + 64 * 4 + 4 * 8;
+    if (from_g && !needs_mt && c >= 1) b += (size_t)8 << (g + c);
     if (needs_mt) b += 65536;
     return b;
 }
@@ -374,7 +439,7 @@ int make_pass(int k_lo, int g, int c, int uf, int mode, int g_f, PassTableFn src
     p->mode = mode;
     p->g_f = g_f;
     p->needs_mt = (uf > 0) || mode == 2;
-    p->smem = pass_smem(g, c, uf, p->needs_mt);
+    p->smem = pass_smem(g, c, uf, p->needs_mt, false);
     p->threads = std::max(32, std::min(512, (1 << (g + c)) / 2));
     return 0;
 }
@@ -474,7 +539,8 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
     a.strideF = strideF;
     a.strideW = strideW;
     const uint64_t tiles = ((1ull << M) >> (p.g + p.c)) * (uint64_t)count;
-    k_fft_pass<<<(unsigned)std::min<uint64_t>(tiles, num_sms()), p.threads, p.smem, s>>>(a);
+    const size_t smem = pass_smem(p.g, p.c, p.uf, p.needs_mt, g64 != nullptr);
+    k_fft_pass<<<(unsigned)std::min<uint64_t>(tiles, num_sms()), p.threads, smem, s>>>(a);
     return 0;
 }
 

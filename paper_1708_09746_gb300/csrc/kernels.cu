@@ -78,14 +78,87 @@ __global__ void k_bcvt_level(T *f, uint64_t n_half, int logE, int loge, int inve
     }
 }
 
+// A run of G consecutive levels (a, a - K), a = a_top .. a_top - G + 1, in
+// one sweep over a shared-memory tile.  Every XOR of level a joins indices
+// that differ by E - e = 2^(a - a_low) S, S = (2^K - 1) 2^(a_low - K), inside
+// the aligned segments of Z = 2^(a_top + 1) elements, so each segment splits
+// into the classes {r + n S : r + n S < Z}, r < S, which the G levels never
+// mix (at most ceil(Z / S) <= RM rows; the host picks G so that they fit).  A
+// thread loads one class into registers, applies the G divisions with the
+// exact step conditions of each row's position, and stores it back: one
+// shared-memory round trip per run instead of one per level.
+template <typename T, int G, int RM, bool INV>
+__device__ __forceinline__ void bcvt_run(T *s, uint32_t tile, int a_top, int K) {
+    const int a_low = a_top - G + 1;
+    const uint32_t S = ((1u << K) - 1) << (a_low - K);
+    const uint32_t Z = 1u << (a_top + 1);
+    const uint32_t items = (tile >> (a_top + 1)) * S;
+    for (uint32_t q = threadIdx.x; q < items; q += blockDim.x) {
+        const uint32_t seg = q / S, r = q - seg * S;
+        T *const sb = s + seg * Z + r;
+        T v[RM];
+        uint32_t valid = 0;  // bit n: row n lies inside the segment
+#pragma unroll
+        for (int n = 0; n < RM; n++) {
+            if (r + (uint32_t)n * S < Z) {
+                valid |= 1u << n;
+                v[n] = sb[n * S];
+            } else {
+                memset(&v[n], 0, sizeof(T));
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < G; it++) {
+            const int jj = INV ? it : G - 1 - it;  // row distance 2^jj
+            const int a = a_low + jj;
+            const uint32_t E = 1u << a, e = 1u << (a - K), msk = 2 * E - 1;
+#pragma unroll
+            for (int st = 0; st < 2; st++) {
+                const bool step1 = (st == 0) != INV;  // forward: step 1 then 2
+#pragma unroll
+                for (int n = 0; n + (1 << jj) < RM; n++) {
+                    // a receiver's partner lies in the same level segment,
+                    // so a valid receiver always has a valid source
+                    const uint32_t o = (r + (uint32_t)n * S) & msk;
+                    const bool act = ((valid >> n) & 1u) && (step1 ? (o - E < e) : (o - e < E - e));
+                    if (act) v[n] = xr(v[n], v[n + (1 << jj)]);
+                }
+            }
+        }
+#pragma unroll
+        for (int n = 0; n < RM; n++)
+            if ((valid >> n) & 1u) sb[n * S] = v[n];
+    }
+}
+
+// Rows of one class for a run of G levels with step K: ceil(2^(G+K) / (2^K - 1)).
+__host__ __device__ constexpr int run_rows(int G, int K) {
+    return (int)((((1u << (G + K)) + (1u << K) - 2) / ((1u << K) - 1)));
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void bcvt_run_any(T *s, uint32_t tile, int a_top, int K, int G) {
+    switch (G) {
+        case 1: bcvt_run<T, 1, 4, INV>(s, tile, a_top, K); break;
+        case 2: bcvt_run<T, 2, 6, INV>(s, tile, a_top, K); break;
+        case 3:
+            if constexpr (sizeof(T) == 8)
+                bcvt_run<T, 3, 10, INV>(s, tile, a_top, K);
+            else
+                bcvt_run<T, 3, 9, INV>(s, tile, a_top, K);
+            break;
+        default: break;
+    }
+}
+
 // A strided tile: index bits [0, c) ("columns", consecutive in memory) and
 // [lo, lo + w) ("rows"); the other bits name the CTA.  A level whose mixing
 // bits [loge, logE] lie inside the rows acts on the tile-local index
 // (row << c) | col exactly as on the global index, with logE and loge moved
-// by c - lo (the levels in `lb` are given in tile-local form).
+// by c - lo (the runs in `lb` are given in tile-local form).
 template <typename T>
-__global__ void k_bcvt_tile(T *f, int c, int lo, int w, LevelBatch lb, int inverse,
-                            uint64_t stride) {
+__global__ void __launch_bounds__(512, 1) k_bcvt_tile(T *f, int c, int lo, int w, LevelBatch lb,
+                                                      int inverse, uint64_t stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s = reinterpret_cast<T *>(smem_raw);
     f += blockIdx.y * stride;
@@ -95,16 +168,27 @@ __global__ void k_bcvt_tile(T *f, int c, int lo, int w, LevelBatch lb, int inver
     const uint64_t hi = (uint64_t)blockIdx.x >> mid_bits;
     const uint64_t base = (hi << (lo + w)) | (mid << c);
     const uint32_t cmask = (1u << c) - 1;
-    for (uint32_t i = threadIdx.x; i < tile; i += blockDim.x)
-        s[i] = f[base | ((uint64_t)(i >> c) << lo) | (i & cmask)];
+    // U independent loads per thread in flight (the tile is one CTA's only work)
+    constexpr int U = sizeof(T) == 8 ? 16 : 8;
+    for (uint32_t i0 = threadIdx.x; i0 < tile; i0 += U * blockDim.x) {
+        T v[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t i = i0 + u * blockDim.x;
+            if (i < tile) v[u] = f[base | ((uint64_t)(i >> c) << lo) | (i & cmask)];
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t i = i0 + u * blockDim.x;
+            if (i < tile) s[i] = v[u];
+        }
+    }
     __syncthreads();
     for (int L = 0; L < lb.count; L++) {
-        const int logE = lb.logE[L], loge = lb.loge[L];
-        const uint32_t E = 1u << logE, e = 1u << loge;
-        for (uint32_t q = threadIdx.x; q < tile / 2; q += blockDim.x) {
-            uint32_t seg = q >> logE, t = q & (E - 1);
-            if (t < E - e) bcvt_item(s, (uint64_t)seg << (logE + 1), E, e, t, inverse);
-        }
+        if (inverse)
+            bcvt_run_any<T, true>(s, tile, lb.a_top[L], lb.K[L], lb.G[L]);
+        else
+            bcvt_run_any<T, false>(s, tile, lb.a_top[L], lb.K[L], lb.G[L]);
         __syncthreads();
     }
     for (uint32_t i = threadIdx.x; i < tile; i += blockDim.x)
@@ -323,6 +407,15 @@ template <typename T>
 static int tile_log_for() {
     return sizeof(T) == 8 ? 14 : 13;
 }
+// Whether a run of G levels with step K fits the register rows that
+// bcvt_run_any gives it (64-bit: 4, 6, 10 rows for G = 1..3; 128-bit: 4, 6,
+// 9 rows).
+template <typename T>
+static bool run_fits(int G, int K) {
+    static const int rows64[4] = {0, 4, 6, 10}, rows128[4] = {0, 4, 6, 9};
+    if (G > 3) return false;
+    return run_rows(G, K) <= (sizeof(T) == 8 ? rows64[G] : rows128[G]);
+}
 template <typename T>
 static int min_cols_for() {
     return sizeof(T) == 8 ? 4 : 3;
@@ -412,12 +505,23 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
             c = std::min(glo, budget - w);
             lo = glo;
         }
+        // group the tile's levels into runs of consecutive a with one K
         LevelBatch lb{};
         lb.count = 0;
-        for (int q = i; q < j; q++) {
-            lb.logE[lb.count] = (int8_t)(lv.v[q].logE - lo + c);
-            lb.loge[lb.count] = (int8_t)(lv.v[q].loge - lo + c);
+        const int dir = inverse ? 1 : -1;  // order of a within a run
+        for (int q = i; q < j;) {
+            const int K = lv.v[q].logE - lv.v[q].loge;
+            int g = 1;
+            while (q + g < j && run_fits<T>(g + 1, K) &&
+                   lv.v[q + g].logE - lv.v[q + g].loge == K &&
+                   lv.v[q + g].logE == lv.v[q].logE + dir * g)
+                g++;
+            const int top = inverse ? lv.v[q + g - 1].logE : lv.v[q].logE;
+            lb.a_top[lb.count] = (int8_t)(top - lo + c);
+            lb.K[lb.count] = (int8_t)K;
+            lb.G[lb.count] = (int8_t)g;
             lb.count++;
+            q += g;
         }
         size_t smem = sizeof(T) << (c + w);
         int threads = std::max(32, std::min(512, 1 << (c + w - 1)));

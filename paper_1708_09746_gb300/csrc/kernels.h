@@ -10,12 +10,16 @@ namespace gf2x {
 
 struct DevTables;
 
-// Consecutive BasisCvt levels applied inside one shared-memory tile.
+// Consecutive BasisCvt levels applied inside one shared-memory tile, grouped
+// into runs: run i is the G[i] levels (a, a - K[i]) for a = a_top[i] down to
+// a_top[i] - G[i] + 1 (tile-local index bits), listed in the order they are
+// applied (the inverse applies each run's levels bottom-up); G <= 3.
 struct LevelBatch {
     static constexpr int kMax = 48;
     int count;
-    int8_t logE[kMax];
-    int8_t loge[kMax];
+    int8_t a_top[kMax];
+    int8_t K[kMax];
+    int8_t G[kMax];
 };
 
 // One operand of a product as Split reads it: nw words, the last one masked.
