@@ -25,6 +25,11 @@ namespace {
 struct DeviceCtx {
     DevTables *tables = nullptr;
     int *status = nullptr;  // device status word of the pipelined kernels
+    // Workspace pool: keeps its memory mapped between products (release
+    // threshold at the maximum), so that a product does not map and unmap the
+    // pages of its workspace every time.
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t copy_stream = nullptr;  // second operand's upload in gf2x_mul_host
 };
 
 std::mutex g_ctx_mu;
@@ -71,6 +76,58 @@ int get_tables(const DevTables **out) {
     }
     *out = c.tables;
     return GF2X_OK;
+}
+
+// The workspace pool and the copy stream of the current device, created on
+// first use.
+int device_pool(cudaMemPool_t *pool, cudaStream_t *copy_stream) {
+    int dev;
+    int rc = current_device(&dev);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    DeviceCtx &c = g_ctx[dev];
+    if (!c.pool) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pl = nullptr;
+        if (cudaMemPoolCreate(&pl, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return GF2X_ECUDA;
+        }
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pl, cudaMemPoolAttrReleaseThreshold, &keep);
+        cudaStream_t cs = nullptr;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            cudaMemPoolDestroy(pl);
+            return GF2X_ECUDA;
+        }
+        c.pool = pl;
+        c.copy_stream = cs;
+    }
+    if (pool) *pool = c.pool;
+    if (copy_stream) *copy_stream = c.copy_stream;
+    return GF2X_OK;
+}
+
+// Stream-ordered workspace from the device's pool.
+int ws_alloc(void **p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool;
+    int rc = device_pool(&pool, nullptr);
+    if (rc) return rc;
+    if (cudaMallocFromPoolAsync(p, bytes ? bytes : 256, pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return GF2X_ENOMEM;
+    }
+    return GF2X_OK;
+}
+
+void ws_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
 }
 
 // Device status word of the current device (valid after get_tables).
@@ -180,12 +237,12 @@ int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits) {
 
 // Alg. 5, stage after stage, on `s`, with the library's tables.
 int plan_run(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out, void *ws,
-             cudaStream_t s) {
+             cudaStream_t s, cudaEvent_t b_ready = nullptr) {
     const DevTables *T;
     int rc = get_tables(&T);
     if (rc) return rc;
     StageTimer tm(s);
-    rc = plan_run_core(p, a, b, out, ws, s, T, device_status(), &tm);
+    rc = plan_run_core(p, a, b, out, ws, s, T, device_status(), &tm, b_ready);
     return rc ? GF2X_ECUDA : GF2X_OK;
 }
 
@@ -237,12 +294,9 @@ int mul_on_stream(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64
     int rc = cached_plan(na_bits, nb_bits, &p);
     if (rc) return rc;
     void *ws = nullptr;
-    if (cudaMallocAsync(&ws, p->ws_bytes, s) != cudaSuccess) {
-        cudaGetLastError();
-        return GF2X_ENOMEM;
-    }
+    if ((rc = ws_alloc(&ws, p->ws_bytes, s))) return rc;
     rc = plan_run(p.get(), a, b, out, ws, s);
-    cudaFreeAsync(ws, s);
+    ws_free(ws, s);
     if (rc == GF2X_OK) rc = check_launch();
     return rc;
 }
@@ -262,6 +316,8 @@ int check_product_args(const uint64_t *a, uint64_t na_bits, const uint64_t *b, u
     return check_operands(a, na_bits, b, nb_bits, out);
 }
 StageHook *new_timer(cudaStream_t s) { return new StageTimer(s); }
+int ws_alloc(void **p, size_t bytes, cudaStream_t s) { return ::ws_alloc(p, bytes, s); }
+void ws_free(void *p, cudaStream_t s) { ::ws_free(p, s); }
 int run_one(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out, void *ws,
             cudaStream_t s) {
     return plan_run(p, a, b, out, ws, s);
@@ -331,22 +387,37 @@ int gf2x_mul_host(const uint64_t *a_host, uint64_t na_bits, const uint64_t *b_ho
         size_t bo = 8 * gf2x_out_words(na_bits, nb_bits);
         std::shared_ptr<gf2x_plan> p;
         if ((rc = cached_plan(na_bits, nb_bits, &p))) return rc;
+        cudaStream_t cs;
+        if ((rc = device_pool(nullptr, &cs))) return rc;
         char *buf = nullptr;
         size_t total = p->ws_bytes + ((ba + 255) & ~255ull) + ((bb + 255) & ~255ull) + bo;
-        if (cudaMallocAsync(reinterpret_cast<void **>(&buf), total, s) != cudaSuccess) {
-            cudaGetLastError();
-            return GF2X_ENOMEM;
-        }
+        if ((rc = ws_alloc(reinterpret_cast<void **>(&buf), total, s))) return rc;
         uint64_t *da = reinterpret_cast<uint64_t *>(buf + p->ws_bytes);
         uint64_t *db = reinterpret_cast<uint64_t *>(buf + p->ws_bytes + ((ba + 255) & ~255ull));
         uint64_t *dout = reinterpret_cast<uint64_t *>(buf + p->ws_bytes + ((ba + 255) & ~255ull) +
                                                       ((bb + 255) & ~255ull));
+        // b is uploaded on the copy stream while a is split, converted and
+        // transformed on s; the product path waits for it before Split(b).
+        cudaEvent_t alloc_done = nullptr, b_ready = nullptr;
+        if (cudaEventCreateWithFlags(&alloc_done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b_ready, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (alloc_done) cudaEventDestroy(alloc_done);
+            ws_free(buf, s);
+            return GF2X_ECUDA;
+        }
+        cudaEventRecord(alloc_done, s);
         cudaMemcpyAsync(da, a_host, ba, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(db, b_host, bb, cudaMemcpyHostToDevice, s);
-        rc = plan_run(p.get(), da, db, dout, buf, s);
+        cudaStreamWaitEvent(cs, alloc_done, 0);
+        cudaMemcpyAsync(db, b_host, bb, cudaMemcpyHostToDevice, cs);
+        cudaEventRecord(b_ready, cs);
+        rc = plan_run(p.get(), da, db, dout, buf, s, b_ready);
         cudaMemcpyAsync(out_host, dout, bo, cudaMemcpyDeviceToHost, s);
-        cudaFreeAsync(buf, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) {
+        ws_free(buf, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        cudaEventDestroy(alloc_done);
+        cudaEventDestroy(b_ready);
+        if (e != cudaSuccess) {
             cudaGetLastError();
             return GF2X_ECUDA;
         }
@@ -589,6 +660,19 @@ int gf2x_shutdown(void) {
             cudaDeviceSynchronize();
             cudaFree(kv.second.tables);
             kv.second.tables = nullptr;
+        }
+        if (kv.second.status) {
+            cudaSetDevice(kv.first);
+            cudaFree(kv.second.status);
+            kv.second.status = nullptr;
+        }
+        if (kv.second.pool) {
+            cudaSetDevice(kv.first);
+            cudaDeviceSynchronize();
+            cudaStreamDestroy(kv.second.copy_stream);
+            cudaMemPoolDestroy(kv.second.pool);
+            kv.second.pool = nullptr;
+            kv.second.copy_stream = nullptr;
         }
     }
     if (cur >= 0) cudaSetDevice(cur);

@@ -20,6 +20,10 @@ int check_product_args(const uint64_t *a, uint64_t na_bits, const uint64_t *b, u
                        const uint64_t *out);
 // Per-stage timer feeding gf2x_profile_read (records only while profiling is on).
 StageHook *new_timer(cudaStream_t s);
+// Stream-ordered workspace from the library's pool of the current device
+// (memory stays mapped between calls).
+int ws_alloc(void **p, size_t bytes, cudaStream_t s);
+void ws_free(void *p, cudaStream_t s);
 // One product with plan p and workspace ws on stream s.
 int run_one(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out, void *ws,
             cudaStream_t s);

@@ -162,10 +162,7 @@ int gf2x_mul_batched(int count, const uint64_t *const *a, const uint64_t *na_bit
         char *mem = nullptr;
         const size_t dbytes = n * (2 * sizeof(OperandDesc) + sizeof(OutputDesc));
         const size_t ws_off = (dbytes + 255) & ~(size_t)255;
-        if (cudaMallocAsync(reinterpret_cast<void **>(&mem), ws_off + B.ws_bytes, s) != cudaSuccess) {
-            cudaGetLastError();
-            return GF2X_ENOMEM;
-        }
+        if ((rc = api::ws_alloc(reinterpret_cast<void **>(&mem), ws_off + B.ws_bytes, s))) return rc;
         OperandDesc *da = reinterpret_cast<OperandDesc *>(mem);
         OperandDesc *db = da + n;
         OutputDesc *dout = reinterpret_cast<OutputDesc *>(db + n);
@@ -175,7 +172,7 @@ int gf2x_mul_batched(int count, const uint64_t *const *a, const uint64_t *na_bit
         cudaMemcpyAsync(dout, ho.data(), n * sizeof(OutputDesc), cudaMemcpyHostToDevice, s);
         std::unique_ptr<StageHook> tm(api::new_timer(s));
         rc = enqueue_chunks(&B, da, db, dout, mem + ws_off, s, tm.get());
-        cudaFreeAsync(mem, s);
+        api::ws_free(mem, s);
         if (rc == GF2X_OK && cudaGetLastError() != cudaSuccess) rc = GF2X_ECUDA;
         return rc;
     } catch (const std::bad_alloc &) {

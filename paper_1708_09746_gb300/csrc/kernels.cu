@@ -93,9 +93,28 @@ __device__ __forceinline__ void bcvt_run(T *s, uint32_t tile, int a_top, int K) 
     const uint32_t S = ((1u << K) - 1) << (a_low - K);
     const uint32_t Z = 1u << (a_top + 1);
     const uint32_t items = (tile >> (a_top + 1)) * S;
+    // Classes r >= 2^G e_low (e_low = 2^(a_low - K)) are interior: writing
+    // r + n S = n 2^a_low + (r - n e_low), row n sits at (n mod 2^(jj+1))
+    // 2^a_low + (r - n e_low) in its level segment, so step 1 never applies
+    // and step 2 applies exactly to the rows with bit jj of n clear: the run is
+    // a superset-sum over the G row bits (order-free, its own inverse).
+    const uint32_t r_int = (1u << G) << (a_low - K);
     for (uint32_t q = threadIdx.x; q < items; q += blockDim.x) {
         const uint32_t seg = q / S, r = q - seg * S;
         T *const sb = s + seg * Z + r;
+        if (r >= r_int) {
+            T v[1 << G];
+#pragma unroll
+            for (int n = 0; n < (1 << G); n++) v[n] = sb[n * S];
+#pragma unroll
+            for (int jj = 0; jj < G; jj++)
+#pragma unroll
+                for (int n = 0; n < (1 << G); n++)
+                    if (!((n >> jj) & 1)) v[n] = xr(v[n], v[n + (1 << jj)]);
+#pragma unroll
+            for (int n = 0; n < (1 << G); n++) sb[n * S] = v[n];
+            continue;
+        }
         T v[RM];
         uint32_t valid = 0;  // bit n: row n lies inside the segment
 #pragma unroll
@@ -151,11 +170,73 @@ __device__ __forceinline__ void bcvt_run_any(T *s, uint32_t tile, int a_top, int
     }
 }
 
+// One division by x^E + x^e on every segment of 2E registers of v (Alg. 2
+// steps 1 and 2; the inverse undoes step 2 first).
+template <int N, int E, int e, bool INV, typename T>
+__device__ __forceinline__ void div_regs(T (&v)[N]) {
+#pragma unroll
+    for (int s0 = 0; s0 < N; s0 += 2 * E) {
+        if (!INV) {
+#pragma unroll
+            for (int q = 0; q < e; q++) v[s0 + E + q] = xr(v[s0 + E + q], v[s0 + 2 * E - e + q]);
+#pragma unroll
+            for (int t = 0; t < E - e; t++) v[s0 + e + t] = xr(v[s0 + e + t], v[s0 + E + t]);
+        } else {
+#pragma unroll
+            for (int t = 0; t < E - e; t++) v[s0 + e + t] = xr(v[s0 + e + t], v[s0 + E + t]);
+#pragma unroll
+            for (int q = 0; q < e; q++) v[s0 + E + q] = xr(v[s0 + E + q], v[s0 + 2 * E - e + q]);
+        }
+    }
+}
+
+// The whole BasisCvt of M = 2 or 4 index bits at scale sc (Alg. 3 on 2^M
+// coefficients spaced 2^sc apart): a thread holds one group in registers and
+// applies its divisions, known at compile time.  For M = 4 they are
+// (x^8 + x^2), (x^4 + x) on each half, then (x^8 + x^4) and (x^2 + x) on each
+// quarter; for M = 2 the single (x^2 + x).
+template <typename T, int M, bool INV>
+__device__ __forceinline__ void bcvt_sub(T *s, uint32_t tile, int sc) {
+    constexpr int N = 1 << M;
+    const uint32_t groups = tile >> M, lowmask = (1u << sc) - 1;
+    for (uint32_t q = threadIdx.x; q < groups; q += blockDim.x) {
+        T *const sb = s + (((q >> sc) << (sc + M)) | (q & lowmask));
+        T v[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) v[i] = sb[i << sc];
+        if constexpr (M == 2) {
+            div_regs<4, 2, 1, INV>(v);
+        } else if constexpr (!INV) {
+            div_regs<16, 8, 2, false>(v);
+            div_regs<16, 4, 1, false>(v);
+            div_regs<16, 8, 4, false>(v);
+            div_regs<16, 2, 1, false>(v);
+        } else {
+            div_regs<16, 2, 1, true>(v);
+            div_regs<16, 8, 4, true>(v);
+            div_regs<16, 4, 1, true>(v);
+            div_regs<16, 8, 2, true>(v);
+        }
+#pragma unroll
+        for (int i = 0; i < N; i++) sb[i << sc] = v[i];
+    }
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void bcvt_op(T *s, uint32_t tile, const BcvtOp &op) {
+    if (op.kind == 1)
+        bcvt_sub<T, 2, INV>(s, tile, op.a_top);
+    else if (op.kind == 2)
+        bcvt_sub<T, 4, INV>(s, tile, op.a_top);
+    else
+        bcvt_run_any<T, INV>(s, tile, op.a_top, op.K, op.G);
+}
+
 // A strided tile: index bits [0, c) ("columns", consecutive in memory) and
 // [lo, lo + w) ("rows"); the other bits name the CTA.  A level whose mixing
 // bits [loge, logE] lie inside the rows acts on the tile-local index
 // (row << c) | col exactly as on the global index, with logE and loge moved
-// by c - lo (the runs in `lb` are given in tile-local form).
+// by c - lo (the steps in `lb` are given in tile-local form).
 template <typename T>
 __global__ void __launch_bounds__(512, 1) k_bcvt_tile(T *f, int c, int lo, int w, LevelBatch lb,
                                                       int inverse, uint64_t stride) {
@@ -186,9 +267,9 @@ __global__ void __launch_bounds__(512, 1) k_bcvt_tile(T *f, int c, int lo, int w
     __syncthreads();
     for (int L = 0; L < lb.count; L++) {
         if (inverse)
-            bcvt_run_any<T, true>(s, tile, lb.a_top[L], lb.K[L], lb.G[L]);
+            bcvt_op<T, true>(s, tile, lb.op[L]);
         else
-            bcvt_run_any<T, false>(s, tile, lb.a_top[L], lb.K[L], lb.G[L]);
+            bcvt_op<T, false>(s, tile, lb.op[L]);
         __syncthreads();
     }
     for (uint32_t i = threadIdx.x; i < tile; i += blockDim.x)
@@ -407,15 +488,6 @@ template <typename T>
 static int tile_log_for() {
     return sizeof(T) == 8 ? 14 : 13;
 }
-// Whether a run of G levels with step K fits the register rows that
-// bcvt_run_any gives it (64-bit: 4, 6, 10 rows for G = 1..3; 128-bit: 4, 6,
-// 9 rows).
-template <typename T>
-static bool run_fits(int G, int K) {
-    static const int rows64[4] = {0, 4, 6, 10}, rows128[4] = {0, 4, 6, 9};
-    if (G > 3) return false;
-    return run_rows(G, K) <= (sizeof(T) == 8 ? rows64[G] : rows128[G]);
-}
 template <typename T>
 static int min_cols_for() {
     return sizeof(T) == 8 ? 4 : 3;
@@ -452,11 +524,72 @@ static void launch_bcvt_top(T *f, int h, int inverse, cudaStream_t s, int count,
     }
 }
 
-// Greedy schedule: consecutive levels whose mixing ranges [loge, logE] fit one
-// tile together (with >= min_cols low column bits, or contiguous) share one
-// pass; a level too wide for any tile is a streaming pass of its own.  The
-// top VarSubs of sizes 2^17 .. 2^24 is one k_bcvt_top pass (first in the
-// forward direction, last in the inverse).
+// Steps of a BasisCvt of 2^m coefficients in forward order (global index
+// bits), from the recursion of Alg. 3: a node of 2 or 4 bits is one
+// register transform; a larger node's VarSubs divisions (a, a - K) become
+// runs of at most max_g(K, a) levels, followed by its two children.
+struct OpList {
+    static constexpr int kMax = 64;
+    int n = 0;
+    BcvtOp v[kMax];
+    bool push(BcvtOp o) {
+        if (n >= kMax) return false;
+        v[n++] = o;
+        return true;
+    }
+};
+
+template <typename F>
+static bool ops_rec(int m, int sc, OpList &out, const F &max_g) {
+    if (m <= 1) return true;
+    if (m == 2) return out.push(BcvtOp{1, (int8_t)sc, 1, 1});
+    if (m == 4) return out.push(BcvtOp{2, (int8_t)sc, 2, 4});
+    int K = 1;
+    while (2 * K <= m - 1) K *= 2;
+    for (int a = m - 1 + sc, left = m - K; left > 0;) {
+        const int g = std::min(left, max_g(K, a));
+        if (!out.push(BcvtOp{0, (int8_t)a, (int8_t)K, (int8_t)g})) return false;
+        a -= g;
+        left -= g;
+    }
+    return ops_rec(m - K, sc + K, out, max_g) && ops_rec(K, sc, out, max_g);
+}
+
+// The divisions (logE, loge) of a step, in forward order.
+static int op_levels(const BcvtOp &o, Level *lv) {
+    const int s = o.a_top;
+    if (o.kind == 1) {
+        lv[0] = Level{(int8_t)(s + 1), (int8_t)s};
+        return 1;
+    }
+    if (o.kind == 2) {
+        lv[0] = Level{(int8_t)(s + 3), (int8_t)(s + 1)};
+        lv[1] = Level{(int8_t)(s + 2), (int8_t)s};
+        lv[2] = Level{(int8_t)(s + 3), (int8_t)(s + 2)};
+        lv[3] = Level{(int8_t)(s + 1), (int8_t)s};
+        return 4;
+    }
+    for (int i = 0; i < o.G; i++) lv[i] = Level{(int8_t)(o.a_top - i), (int8_t)(o.a_top - i - o.K)};
+    return o.G;
+}
+
+static void op_range(const BcvtOp &o, int *lo, int *hi) {
+    Level lv[4];
+    const int k = op_levels(o, lv);
+    *lo = 64;
+    *hi = -1;
+    for (int i = 0; i < k; i++) {
+        *lo = std::min(*lo, (int)lv[i].loge);
+        *hi = std::max(*hi, (int)lv[i].logE);
+    }
+}
+
+// Tile passes: consecutive steps whose index ranges fit one tile together
+// (>= min_cols low column bits, or contiguous) share one pass; a step too wide
+// for any tile runs as streaming passes, one per division.  The top VarSubs
+// of sizes 2^17 .. 2^24 is one k_bcvt_top pass (first in the forward
+// direction, last in the inverse).  The steps are checked against the level
+// list `fwd` (the divisions of Alg. 3 in order) before anything is launched.
 template <typename T>
 uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStream_t s, int count,
                        uint64_t stride) {
@@ -464,35 +597,69 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
                      (int)(sizeof(T) << tile_log_for<T>()));
     uint64_t launches = 0;
     const int h_top = top_levels(m, fwd);
-    LevelList lv;
-    for (int q = 0; q < fwd.n - h_top; q++)
-        lv.push(fwd.v[inverse ? fwd.n - 1 - q : h_top + q]);
-    if (h_top && !inverse) {
-        launch_bcvt_top<T>(f, h_top, 0, s, count, stride);
-        launches++;
-    }
     const int budget = std::min(tile_log_for<T>(), m), cmin = min_cols_for<T>();
     const uint64_t n = 1ull << m;
     auto fits = [&](int glo, int ghi) {
         if (ghi + 1 <= budget) return true;
         return glo >= cmin && (ghi - glo + 1) + cmin <= budget;
     };
-    int i = 0;
-    while (i < lv.n) {
-        int glo = lv.v[i].loge, ghi = lv.v[i].logE;
-        if (!fits(glo, ghi)) {
+    // longest register run: 2 levels for K <= 4 (more interior classes), 3
+    // otherwise, fewer if the run would not fit a tile
+    auto max_g = [&](int K, int a) {
+        int g = K <= 4 ? 2 : 3;
+        while (g > 1 && !(a + 1 <= budget || K + g + cmin <= budget)) g--;
+        return g;
+    };
+    OpList ops;
+    bool ok = h_top ? (ops_rec(m - 16, 16, ops, max_g) && ops_rec(16, 0, ops, max_g))
+                    : ops_rec(m, 0, ops, max_g);
+    {  // the steps must expand to exactly the remaining divisions of fwd
+        int q = h_top;
+        for (int i = 0; ok && i < ops.n; i++) {
+            Level lv[4];
+            const int k = op_levels(ops.v[i], lv);
+            for (int t = 0; ok && t < k; t++, q++)
+                ok = q < fwd.n && fwd.v[q].logE == lv[t].logE && fwd.v[q].loge == lv[t].loge;
+        }
+        ok = ok && q == fwd.n;
+    }
+    if (!ok) {  // not expected: apply the divisions one by one
+        for (int q = 0; q < fwd.n; q++) {
+            const Level &L = fwd.v[inverse ? fwd.n - 1 - q : q];
             dim3 grid(grid_for(n / 2, 256, count), count);
-            k_bcvt_level<T><<<grid, 256, 0, s>>>(f, n / 2, lv.v[i].logE, lv.v[i].loge, inverse,
-                                                 stride);
+            k_bcvt_level<T><<<grid, 256, 0, s>>>(f, n / 2, L.logE, L.loge, inverse, stride);
             launches++;
+        }
+        return launches;
+    }
+    if (h_top && !inverse) {
+        launch_bcvt_top<T>(f, h_top, 0, s, count, stride);
+        launches++;
+    }
+    auto op_at = [&](int i) -> const BcvtOp & { return ops.v[inverse ? ops.n - 1 - i : i]; };
+    int i = 0;
+    while (i < ops.n) {
+        int glo, ghi;
+        op_range(op_at(i), &glo, &ghi);
+        if (!fits(glo, ghi)) {
+            Level lv[4];
+            const int k = op_levels(op_at(i), lv);
+            for (int t = 0; t < k; t++) {
+                const Level &L = lv[inverse ? k - 1 - t : t];
+                dim3 grid(grid_for(n / 2, 256, count), count);
+                k_bcvt_level<T><<<grid, 256, 0, s>>>(f, n / 2, L.logE, L.loge, inverse, stride);
+                launches++;
+            }
             i++;
             continue;
         }
         int j = i + 1;
-        while (j < lv.n && j - i < LevelBatch::kMax &&
-               fits(std::min(glo, (int)lv.v[j].loge), std::max(ghi, (int)lv.v[j].logE))) {
-            glo = std::min(glo, (int)lv.v[j].loge);
-            ghi = std::max(ghi, (int)lv.v[j].logE);
+        while (j < ops.n && j - i < LevelBatch::kMax) {
+            int lo2, hi2;
+            op_range(op_at(j), &lo2, &hi2);
+            if (!fits(std::min(glo, lo2), std::max(ghi, hi2))) break;
+            glo = std::min(glo, lo2);
+            ghi = std::max(ghi, hi2);
             j++;
         }
         int c, lo, w;
@@ -505,23 +672,12 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
             c = std::min(glo, budget - w);
             lo = glo;
         }
-        // group the tile's levels into runs of consecutive a with one K
         LevelBatch lb{};
-        lb.count = 0;
-        const int dir = inverse ? 1 : -1;  // order of a within a run
-        for (int q = i; q < j;) {
-            const int K = lv.v[q].logE - lv.v[q].loge;
-            int g = 1;
-            while (q + g < j && run_fits<T>(g + 1, K) &&
-                   lv.v[q + g].logE - lv.v[q + g].loge == K &&
-                   lv.v[q + g].logE == lv.v[q].logE + dir * g)
-                g++;
-            const int top = inverse ? lv.v[q + g - 1].logE : lv.v[q].logE;
-            lb.a_top[lb.count] = (int8_t)(top - lo + c);
-            lb.K[lb.count] = (int8_t)K;
-            lb.G[lb.count] = (int8_t)g;
-            lb.count++;
-            q += g;
+        lb.count = j - i;
+        for (int q = i; q < j; q++) {
+            BcvtOp o = op_at(q);
+            o.a_top = (int8_t)(o.a_top - lo + c);  // tile-local index bits
+            lb.op[q - i] = o;
         }
         size_t smem = sizeof(T) << (c + w);
         int threads = std::max(32, std::min(512, 1 << (c + w - 1)));

@@ -10,16 +10,20 @@ namespace gf2x {
 
 struct DevTables;
 
-// Consecutive BasisCvt levels applied inside one shared-memory tile, grouped
-// into runs: run i is the G[i] levels (a, a - K[i]) for a = a_top[i] down to
-// a_top[i] - G[i] + 1 (tile-local index bits), listed in the order they are
-// applied (the inverse applies each run's levels bottom-up); G <= 3.
+// One step of a BasisCvt tile pass, in tile-local index bits:
+//  kind 0: a run of G <= 3 divisions (a, a - K), a = a_top .. a_top - G + 1;
+//  kind 1: the whole BasisCvt of 2 index bits at scale `a_top` (one division);
+//  kind 2: the whole BasisCvt of 4 index bits at scale `a_top` (four divisions).
+struct BcvtOp {
+    int8_t kind, a_top, K, G;
+};
+
+// The steps of one tile pass, in the order they are applied (the inverse
+// lists them reversed and applies each one inverted).
 struct LevelBatch {
     static constexpr int kMax = 48;
     int count;
-    int8_t a_top[kMax];
-    int8_t K[kMax];
-    int8_t G[kMax];
+    BcvtOp op[kMax];
 };
 
 // One operand of a product as Split reads it: nw words, the last one masked.

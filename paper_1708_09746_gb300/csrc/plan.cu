@@ -68,7 +68,7 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
                    const OperandDesc *many_b, const OutputDesc *many_out, const OperandDesc &one_a,
                    const OperandDesc &one_b, const OutputDesc &one_out, uint64_t max_out_words,
                    void *ws, size_t ws_stride, cudaStream_t s, const DevTables *T, int *st,
-                   StageHook *hook) {
+                   StageHook *hook, cudaEvent_t b_ready) {
     char *base = static_cast<char *>(ws);
     uint4 *FA = reinterpret_cast<uint4 *>(base + p->off_fa);
     uint4 *FB = reinterpret_cast<uint4 *>(base + p->off_fb);
@@ -81,25 +81,26 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
     auto end = [&](uint64_t n) {
         if (hook) hook->end(n);
     };
-    uint64_t n;
-    // Split
+    // Split, BasisCvt, changeRepr + FFT_LCH of a (changeRepr fused into the
+    // first pass; the layers above log2 Pa are fan-outs: the pass reads the
+    // blocks periodically)
     begin(ST_SPLIT);
     launch_split_pad(one_a, many_a, count, WA, p->Pa, sW, s);
-    launch_split_pad(one_b, many_b, count, WB, p->Pb, sW, s);
-    end(2);
-    // BasisCvt on the 64-bit blocks
+    end(1);
     begin(ST_BCVT);
-    n = run_basis_cvt<uint64_t>(WA, p->pa_log, p->lv_a, 0, s, count, sW);
-    n += run_basis_cvt<uint64_t>(WB, p->pb_log, p->lv_b, 0, s, count, sW);
-    end(n);
-    // changeRepr + FFT_LCH of a (changeRepr fused into the first pass; the
-    // layers above log2 Pa are fan-outs: the pass reads the blocks periodically)
+    end(run_basis_cvt<uint64_t>(WA, p->pa_log, p->lv_a, 0, s, count, sW));
     begin(ST_FFT_A);
     for (int i = 0; i < p->fft_a.n; i++)
         launch_fft_pass(p->fft_a.v[i], p->M, FA, i == 0 ? WA : nullptr, p->Pa, nullptr, T, st, s,
                         count, sF, sW);
     end(p->fft_a.n);
-    // changeRepr + FFT_LCH of b, top layers
+    // the same for b, then its top FFT layers
+    if (b_ready) cudaStreamWaitEvent(s, b_ready, 0);
+    begin(ST_SPLIT);
+    launch_split_pad(one_b, many_b, count, WB, p->Pb, sW, s);
+    end(1);
+    begin(ST_BCVT);
+    end(run_basis_cvt<uint64_t>(WB, p->pb_log, p->lv_b, 0, s, count, sW));
     begin(ST_FFT_B);
     for (int i = 0; i < p->fft_b.n; i++)
         launch_fft_pass(p->fft_b.v[i], p->M, FB, i == 0 ? WB : nullptr, p->Pb, nullptr, T, st, s,
@@ -117,8 +118,7 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
     end(p->ifft_top.n);
     // iBasisCvt
     begin(ST_IBCVT);
-    n = run_basis_cvt<uint4>(FB, p->M, p->lv_c, 1, s, count, sF);
-    end(n);
+    end(run_basis_cvt<uint4>(FB, p->M, p->lv_c, 1, s, count, sF));
     // changeRepr^-1 + InterleavedCombine
     begin(ST_OUT);
     launch_ichrepr_combine(FB, p->N, sF, one_out, many_out, count,
@@ -131,12 +131,13 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
 uint64_t mask_of_bits(uint64_t bits) { return (bits % 64) ? ((1ull << (bits % 64)) - 1) : ~0ull; }
 
 int plan_run_core(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out,
-                  void *ws, cudaStream_t s, const DevTables *T, int *st, StageHook *hook) {
+                  void *ws, cudaStream_t s, const DevTables *T, int *st, StageHook *hook,
+                  cudaEvent_t b_ready) {
     const OperandDesc da{a, p->na_w, mask_of_bits(p->na_bits)};
     const OperandDesc db{b, p->nb_w, mask_of_bits(p->nb_bits)};
     const OutputDesc dout{out, p->out_words, mask_of_bits(p->total_bits)};
     return plan_run_batch(p, 1, nullptr, nullptr, nullptr, da, db, dout, p->out_words, ws,
-                          p->ws_bytes, s, T, st, hook);
+                          p->ws_bytes, s, T, st, hook, b_ready);
 }
 
 }  // namespace gf2x

@@ -55,8 +55,11 @@ int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits, PassTableFn src)
 
 // Enqueues the whole product on `s` with workspace `ws` (p->ws_bytes bytes,
 // 256-byte aligned), tables T and status word `status`; `hook` may be null.
+// If b_ready is given, the stages of b start after it (b may still be
+// arriving while a is split, converted and transformed).
 int plan_run_core(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out,
-                  void *ws, cudaStream_t s, const DevTables *T, int *status, StageHook *hook);
+                  void *ws, cudaStream_t s, const DevTables *T, int *status, StageHook *hook,
+                  cudaEvent_t b_ready = nullptr);
 
 // `count` products sharing plan p (same M, log2 Pa, log2 Pb): product y's
 // operands and output from many_a[y], many_b[y], many_out[y] (device arrays;
@@ -66,7 +69,7 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
                    const OperandDesc *many_b, const OutputDesc *many_out, const OperandDesc &one_a,
                    const OperandDesc &one_b, const OutputDesc &one_out, uint64_t max_out_words,
                    void *ws, size_t ws_stride, cudaStream_t s, const DevTables *T, int *status,
-                   StageHook *hook);
+                   StageHook *hook, cudaEvent_t b_ready = nullptr);
 
 uint64_t mask_of_bits(uint64_t bits);
 
