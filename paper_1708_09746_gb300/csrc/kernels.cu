@@ -170,6 +170,80 @@ __device__ __forceinline__ void bcvt_run_any(T *s, uint32_t tile, int a_top, int
     }
 }
 
+// A run of G divisions (a, a - K), a = a_top .. a_top - G + 1, as one
+// streaming pass over the whole array (runs too wide for a shared-memory
+// tile: K >= 8).  The classes {r + n S} of bcvt_run are taken straight from
+// global memory, one 32-bit limb of one class per thread (the divisions act
+// bitwise); consecutive threads take consecutive (class, limb) pairs, so every
+// row is read and written in full 128-byte lines.  Interior classes
+// (r >= 2^G e_low) are a superset-sum over the row bits; the others apply the
+// exact step conditions of each row's position.
+template <typename T, int G, int RM, bool INV, bool BND>
+__global__ void __launch_bounds__(256) k_bcvt_class(T *f, int a_top, int K, uint64_t n_el,
+                                                    uint64_t stride) {
+    constexpr int L = sizeof(T) / 4;
+    f += blockIdx.y * stride;
+    uint32_t *const F = reinterpret_cast<uint32_t *>(f);
+    const int a_low = a_top - G + 1;
+    const uint64_t e_low = 1ull << (a_low - K);
+    const uint64_t S = ((1ull << K) - 1) * e_low;
+    const uint64_t Z = 1ull << (a_top + 1);
+    const uint64_t r_int = e_low << G;
+    // this launch's classes in each segment: [0, r_int) or [r_int, S)
+    const uint64_t r0 = BND ? 0 : r_int, nr = BND ? r_int : S - r_int;
+    const uint64_t items = (n_el / Z) * nr * L;
+    const uint64_t rowstep = S * L;
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < items;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t rest = q / L;
+        const uint64_t seg = rest / nr, r = r0 + (rest - seg * nr);
+        uint32_t *const base = F + (seg * Z + r) * L + (q % L);
+        if constexpr (!BND) {
+            uint32_t v[1 << G];
+#pragma unroll
+            for (int n = 0; n < (1 << G); n++) v[n] = base[n * rowstep];
+#pragma unroll
+            for (int jj = 0; jj < G; jj++)
+#pragma unroll
+                for (int n = 0; n < (1 << G); n++)
+                    if (!((n >> jj) & 1)) v[n] ^= v[n + (1 << jj)];
+#pragma unroll
+            for (int n = 0; n < (1 << G); n++) base[n * rowstep] = v[n];
+        } else {
+            uint32_t v[RM];
+            uint32_t valid = 0;
+#pragma unroll
+            for (int n = 0; n < RM; n++) {
+                v[n] = 0;
+                if (r + (uint64_t)n * S < Z) {
+                    valid |= 1u << n;
+                    v[n] = base[n * rowstep];
+                }
+            }
+#pragma unroll
+            for (int it = 0; it < G; it++) {
+                const int jj = INV ? it : G - 1 - it;
+                const int a = a_low + jj;
+                const uint64_t E = 1ull << a, e = 1ull << (a - K), msk = 2 * E - 1;
+#pragma unroll
+                for (int st = 0; st < 2; st++) {
+                    const bool step1 = (st == 0) != INV;
+#pragma unroll
+                    for (int n = 0; n < RM; n++) {
+                        const int p = n + (1 << jj);
+                        if (p >= RM || !((valid >> n) & 1u)) continue;
+                        const uint64_t o = (r + (uint64_t)n * S) & msk;
+                        if (step1 ? (o - E < e) : (o - e < E - e)) v[n] ^= v[p];
+                    }
+                }
+            }
+#pragma unroll
+            for (int n = 0; n < RM; n++)
+                if ((valid >> n) & 1u) base[n * rowstep] = v[n];
+        }
+    }
+}
+
 // One division by x^E + x^e on every segment of 2E registers of v (Alg. 2
 // steps 1 and 2; the inverse undoes step 2 first).
 template <int N, int E, int e, bool INV, typename T>
@@ -584,6 +658,37 @@ static void op_range(const BcvtOp &o, int *lo, int *hi) {
     }
 }
 
+template <typename T>
+static void launch_bcvt_class(T *f, int m, const BcvtOp &o, int inverse, cudaStream_t s, int count,
+                              uint64_t stride) {
+    constexpr int L = sizeof(T) / 4;
+    const uint64_t n = 1ull << m;
+    const int a_low = o.a_top - o.G + 1;
+    const uint64_t e_low = 1ull << (a_low - o.K);
+    const uint64_t S = ((1ull << o.K) - 1) * e_low, r_int = e_low << o.G;
+    const uint64_t segs = n >> (o.a_top + 1);
+    const dim3 gi(grid_for(segs * (S - r_int) * L, 256, count), count);
+    const dim3 gb(grid_for(segs * r_int * L, 256, count), count);
+#define GF2X_CLASS_LAUNCH(GG, INV)                                                              \
+    {                                                                                           \
+        k_bcvt_class<T, GG, (1 << GG) + 1, INV, false><<<gi, 256, 0, s>>>(f, o.a_top, o.K, n,  \
+                                                                          stride);              \
+        k_bcvt_class<T, GG, (1 << GG) + 1, INV, true><<<gb, 256, 0, s>>>(f, o.a_top, o.K, n,   \
+                                                                         stride);               \
+    }
+    switch (o.G * 2 + (inverse ? 1 : 0)) {
+        case 2: GF2X_CLASS_LAUNCH(1, false) break;
+        case 3: GF2X_CLASS_LAUNCH(1, true) break;
+        case 4: GF2X_CLASS_LAUNCH(2, false) break;
+        case 5: GF2X_CLASS_LAUNCH(2, true) break;
+        case 6: GF2X_CLASS_LAUNCH(3, false) break;
+        case 7: GF2X_CLASS_LAUNCH(3, true) break;
+        case 8: GF2X_CLASS_LAUNCH(4, false) break;
+        default: GF2X_CLASS_LAUNCH(4, true) break;
+    }
+#undef GF2X_CLASS_LAUNCH
+}
+
 // Tile passes: consecutive steps whose index ranges fit one tile together
 // (>= min_cols low column bits, or contiguous) share one pass; a step too wide
 // for any tile runs as streaming passes, one per division.  The top VarSubs
@@ -603,9 +708,12 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
         if (ghi + 1 <= budget) return true;
         return glo >= cmin && (ghi - glo + 1) + cmin <= budget;
     };
-    // longest register run: 2 levels for K <= 4 (more interior classes), 3
-    // otherwise, fewer if the run would not fit a tile
+    // runs with K >= 8 that do not fit a contiguous tile are streaming class
+    // passes of up to 4 levels; other runs: 2 levels for K <= 4 (more
+    // interior classes), 3 otherwise, fewer if the run would not fit a tile
+    auto streamed = [&](const BcvtOp &o) { return o.kind == 0 && o.K >= 8 && o.a_top + 1 > budget; };
     auto max_g = [&](int K, int a) {
+        if (K >= 8 && a + 1 > budget) return 4;
         int g = K <= 4 ? 2 : 3;
         while (g > 1 && !(a + 1 <= budget || K + g + cmin <= budget)) g--;
         return g;
@@ -641,6 +749,12 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
     while (i < ops.n) {
         int glo, ghi;
         op_range(op_at(i), &glo, &ghi);
+        if (streamed(op_at(i))) {
+            launch_bcvt_class<T>(f, m, op_at(i), inverse, s, count, stride);
+            launches += 2;
+            i++;
+            continue;
+        }
         if (!fits(glo, ghi)) {
             Level lv[4];
             const int k = op_levels(op_at(i), lv);
@@ -654,7 +768,7 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
             continue;
         }
         int j = i + 1;
-        while (j < ops.n && j - i < LevelBatch::kMax) {
+        while (j < ops.n && j - i < LevelBatch::kMax && !streamed(op_at(j))) {
             int lo2, hi2;
             op_range(op_at(j), &lo2, &hi2);
             if (!fits(std::min(glo, lo2), std::max(ghi, hi2))) break;
@@ -662,14 +776,17 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
             ghi = std::max(ghi, hi2);
             j++;
         }
+        // the smallest tile that holds the steps (at least 2^11 elements):
+        // small tiles let two CTAs share an SM and overlap their phases
+        const int tmin = std::min(m, 11);
         int c, lo, w;
         if (ghi + 1 <= budget) {  // contiguous tile
             c = 0;
             lo = 0;
-            w = budget;
+            w = std::min(budget, std::max(ghi + 1, tmin));
         } else {
             w = ghi - glo + 1;
-            c = std::min(glo, budget - w);
+            c = std::min(std::min(glo, budget - w), std::max(cmin, tmin - w));
             lo = glo;
         }
         LevelBatch lb{};
@@ -680,7 +797,7 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
             lb.op[q - i] = o;
         }
         size_t smem = sizeof(T) << (c + w);
-        int threads = std::max(32, std::min(512, 1 << (c + w - 1)));
+        int threads = std::max(32, std::min(smem > 65536 ? 512 : 256, 1 << (c + w - 1)));
         dim3 grid((unsigned)(n >> (c + w)), count);
         k_bcvt_tile<T><<<grid, threads, smem, s>>>(f, c, lo, w, lb, inverse, stride);
         launches++;
