@@ -47,6 +47,10 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="c1_2^28")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-tune", action="store_true",
+                   help="use the default plan parameters instead of autotuning the shape")
+    p.add_argument("--no-sizes", action="store_true",
+                   help="skip the ms-per-product line for 2^29, 2^30 and 2^32 bits")
     p.add_argument("--no-systems", action="store_true",
                    help="skip the batched and serving measurements")
     p.add_argument("--serve-seconds", type=float, default=3.0)
@@ -256,6 +260,38 @@ def fft_hbm_bytes(N, M, la, lb):
     return b
 
 
+def measure_sizes(G, torch, W, dev, stream, flush):
+    """ms per product (device time, autotuned plan, L2 flushed between
+    products) for the larger single-product workloads."""
+    import numpy as np
+    res = {}
+    for name in ("c1_2^29", "c2_2^30", "c2_2^32"):
+        a, na, b, nb = W.make_workload(name)
+        da = torch.from_numpy(a.view(np.int64)).to(dev)
+        db = torch.from_numpy(b.view(np.int64)).to(dev)
+        del a, b
+        out = torch.empty(G.gf2x_out_words(na, nb), dtype=torch.int64, device=dev)
+        tuned = G.gf2x_autotune(na, nb, 2)
+        evs = []
+        with torch.cuda.stream(stream):
+            for i in range(4):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                G.gf2x_mul_async(da, na, db, nb, out, stream)
+                e1.record(stream)
+                evs.append((e0, e1))
+        stream.synchronize()
+        ms = [e0.elapsed_time(e1) for e0, e1 in evs[1:]]
+        N = G.gf2x_fft_points(na, nb)
+        res[name] = {"bits": [na, nb], "ms": sum(ms) / len(ms), "fft_points": N,
+                     "path_hbm_frac": 240 * N / (sum(ms) / len(ms) / 1e3) / 1e9 /
+                     _peaks().get("hbm_gbs", 6800.0), "plan": tuned}
+        del da, db, out
+        torch.cuda.empty_cache()
+    return res
+
+
 def measure_batched(G, torch, W, dev, stream):
     """4096 products, lengths floor(2^U) with U ~ U[12, 22] per side (seed 7);
     operands are slices of one seeded random-word pool (seed 7)."""
@@ -285,28 +321,44 @@ def measure_batched(G, torch, W, dev, stream):
     stream.synchronize()
     t_loop = e0.elapsed_time(e1) / 1e3
     # batched: one batch, captured once and replayed
-    batch = G.gf2x_batch_create(na, nb, 8 << 30)
-    try:
-        G.gf2x_batch_execute(batch, A, B, outs, stream)
-        stream.synchronize()
-        reps = 3
-        e0.record(stream)
-        for _ in range(reps):
+    def run_batch():
+        batch = G.gf2x_batch_create(na, nb, 8 << 30)
+        try:
             G.gf2x_batch_execute(batch, A, B, outs, stream)
-        e1.record(stream)
-        stream.synchronize()
-        t_batch = e0.elapsed_time(e1) / 1e3 / reps
-    finally:
-        G.gf2x_batch_destroy(batch)
+            stream.synchronize()
+            reps = 3
+            e0.record(stream)
+            for _ in range(reps):
+                G.gf2x_batch_execute(batch, A, B, outs, stream)
+            e1.record(stream)
+            stream.synchronize()
+            return e0.elapsed_time(e1) / 1e3 / reps
+        finally:
+            G.gf2x_batch_destroy(batch)
+    t_default = run_batch()
+    # autotune every transform shape of the batch, then build the batch again
+    def lg(x):
+        return max(0, (int(x) - 1).bit_length())
+    shapes = {}
+    for x, y in zip(na, nb):
+        wa, wb = (x + 63) // 64, (y + 63) // 64
+        shapes.setdefault((lg(max(2, wa + wb - 1)), lg(wa), lg(wb)), (x, y))
+    t0 = time.perf_counter()
+    for x, y in shapes.values():
+        G.gf2x_autotune(x, y, 2)
+    t_tune = time.perf_counter() - t0
+    t_batch = run_batch()
     del pool, A, B, outs
     torch.cuda.empty_cache()
     return {"workload": "4096 products, per-side lengths log-uniform in [2^12, 2^22] bits, "
                         "seed 7", "products": 4096,
             "batched_products_per_s": 4096 / t_batch,
+            "batched_default_params_products_per_s": 4096 / t_default,
             "one_by_one_products_per_s": 4096 / t_loop,
             "speedup": t_loop / t_batch, "unit": "products/s",
-            "method": "gf2x_batch_execute (shape-grouped launches, CUDA graph replay) vs "
-                      "gf2x_mul_async in a loop, device-timed"}
+            "autotune": {"shapes": len(shapes), "seconds": t_tune},
+            "method": "gf2x_batch_execute (shape-grouped launches, CUDA graph replay) with "
+                      "autotuned per-shape plans vs gf2x_mul_async in a loop, device-timed"}
 
 
 def measure_serving(G, torch, W, dev, seconds):
@@ -383,6 +435,9 @@ def run_ours(args):
     out = torch.empty(ow, dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
+
+    # plan parameters for this shape from the autotuner (not timed)
+    tuned = G.gf2x_autotune(na, nb, 3) if not args.no_tune else G.gf2x_tune_get(na, nb)
 
     def step():
         G.gf2x_mul_async(da, na, db, nb, out, stream)
@@ -482,6 +537,9 @@ def run_ours(args):
         "clocks": clk,
         "wall_s_timed": wall,
     }
+    line["config"]["plan"] = tuned
+    if not args.no_sizes and world == 1:
+        line["sizes_ms"] = measure_sizes(G, torch, W, dev, stream, flush)
     if not args.no_systems and world == 1:
         try:
             line["batched"] = measure_batched(G, torch, W, dev, stream)

@@ -81,13 +81,16 @@ GF2X_API int gf2x_mul(const uint64_t *a, uint64_t na_bits, const uint64_t *b,
              uint64_t nb_bits, uint64_t *out);
 
 /* As gf2x_mul, asynchronous on `stream`.  The workspace is allocated and
- * freed stream-ordered on `stream`. */
+ * freed stream-ordered on `stream`, from a per-device pool of the library that
+ * keeps its memory mapped between calls (released by gf2x_shutdown). */
 GF2X_API int gf2x_mul_async(const uint64_t *a, uint64_t na_bits, const uint64_t *b,
                    uint64_t nb_bits, uint64_t *out, gf2x_stream_t stream);
 
 /* As gf2x_mul with HOST buffers a, b, out (pageable or pinned).  The call
  * copies the operands to the device, runs the product and copies the result
- * back, all on `stream`, and returns after the result is in `out`. */
+ * back on `stream`, and returns after the result is in `out`.  b is copied on
+ * a second stream of the library while a is split, converted and transformed
+ * (the copies overlap the work only when the host buffers are pinned). */
 GF2X_API int gf2x_mul_host(const uint64_t *a_host, uint64_t na_bits,
                   const uint64_t *b_host, uint64_t nb_bits, uint64_t *out_host,
                   gf2x_stream_t stream);
@@ -114,6 +117,47 @@ GF2X_API int gf2x_plan_execute(gf2x_plan *p, const uint64_t *a, const uint64_t *
                       uint64_t *out, void *workspace, gf2x_stream_t stream);
 
 GF2X_API int gf2x_plan_destroy(gf2x_plan *p);
+
+/* ---- Autotuning --------------------------------------------------------------
+ * Plans of one transform shape (log2 N, log2 Pa, log2 Pb) share parameters
+ * that change the speed of a product but never its result: the FFT fusion
+ * depth (most butterfly layers one strided pass covers, 1 .. 7), the tile
+ * buffers of the strided FFT passes (1 or 2) and the shape of the BasisCvt
+ * tile passes (log2 of the smallest tile, 4 .. 14, and the threads of a CTA
+ * whose tile is at most 64 KiB, 32 .. 512 in steps of 32).  The defaults are
+ * 7, 2, 11 and 256.  The table is process-wide, keyed by shape
+ * only (the GPUs of one process are taken to be alike); plans made after a
+ * change use the new parameters. */
+typedef struct {
+    int fft_depth;
+    int fft_buffers; /* tile buffers of a strided FFT pass: 2 (one CTA per SM
+                        loads the next tile while it computes) or 1 (two CTAs
+                        per SM take turns) */
+    int bcvt_tile_log;
+    int bcvt_threads;
+    double ms; /* device time of one product measured by gf2x_autotune, or -1 */
+} gf2x_tune_t;
+
+/* Times products of this shape on the current device with candidate
+ * parameters (the fusion depths that give distinct pass schedules with one
+ * and two tile buffers, then the BasisCvt tile shapes with the best of those), `reps` timed runs each after one
+ * warm-up (reps <= 0: 3), on operands of the given sizes in scratch buffers
+ * the call allocates and frees.  Stores the fastest parameters for the shape
+ * and returns them in *best.  Synchronous. */
+GF2X_API int gf2x_autotune(uint64_t na_bits, uint64_t nb_bits, int reps,
+                           gf2x_tune_t *best);
+
+/* The parameters plans of this shape use (the defaults, ms = -1, if it was
+ * never tuned or set). */
+GF2X_API int gf2x_tune_get(uint64_t na_bits, uint64_t nb_bits, gf2x_tune_t *out);
+
+/* Sets the parameters of this shape; GF2X_EINVAL if one is out of range. */
+GF2X_API int gf2x_tune_set(uint64_t na_bits, uint64_t nb_bits, const gf2x_tune_t *t);
+
+/* Writes the table to a text file (one shape per line), or reads one back
+ * (entries merged into the table).  GF2X_EINVAL on a malformed file. */
+GF2X_API int gf2x_tune_save(const char *path);
+GF2X_API int gf2x_tune_load(const char *path);
 
 /* ---- Batched products -----------------------------------------------------*/
 

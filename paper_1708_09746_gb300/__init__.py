@@ -43,6 +43,18 @@ _u64 = ctypes.c_uint64
 _vp = ctypes.c_void_p
 _int = ctypes.c_int
 
+class gf2x_tune_t(ctypes.Structure):
+    """Plan parameters of one transform shape (include/gf2x_gb300.h)."""
+    _fields_ = [("fft_depth", ctypes.c_int), ("fft_buffers", ctypes.c_int),
+                ("bcvt_tile_log", ctypes.c_int), ("bcvt_threads", ctypes.c_int),
+                ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"fft_depth": self.fft_depth, "fft_buffers": self.fft_buffers,
+                "bcvt_tile_log": self.bcvt_tile_log, "bcvt_threads": self.bcvt_threads,
+                "ms": self.ms}
+
+
 _SIGS = {
     "gf2x_strerror": (ctypes.c_char_p, [_int]),
     "gf2x_out_words": (_u64, [_u64, _u64]),
@@ -80,6 +92,11 @@ _SIGS = {
                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64)]),
     "gf2x_server_reset_stats": (_int, [_vp]),
     "gf2x_server_destroy": (_int, [_vp]),
+    "gf2x_autotune": (_int, [_u64, _u64, _int, ctypes.POINTER(gf2x_tune_t)]),
+    "gf2x_tune_get": (_int, [_u64, _u64, ctypes.POINTER(gf2x_tune_t)]),
+    "gf2x_tune_set": (_int, [_u64, _u64, ctypes.POINTER(gf2x_tune_t)]),
+    "gf2x_tune_save": (_int, [ctypes.c_char_p]),
+    "gf2x_tune_load": (_int, [ctypes.c_char_p]),
 }
 
 
@@ -156,6 +173,34 @@ def gf2x_mul_noalloc(a, na_bits, b, nb_bits, out, stream=None):
     is a static device array of the library (see include/gf2x_gb300.h)."""
     _check(load().gf2x_mul_noalloc(_ptr(a), na_bits, _ptr(b), nb_bits, _ptr(out),
                                    _stream(stream)), "gf2x_mul_noalloc")
+
+
+def gf2x_autotune(na_bits, nb_bits, reps=3):
+    """Times candidate plan parameters for this product shape on the current
+    device, stores the fastest for the shape and returns them as a dict."""
+    t = gf2x_tune_t()
+    _check(load().gf2x_autotune(na_bits, nb_bits, int(reps), ctypes.byref(t)), "gf2x_autotune")
+    return t.as_dict()
+
+
+def gf2x_tune_get(na_bits, nb_bits):
+    t = gf2x_tune_t()
+    _check(load().gf2x_tune_get(na_bits, nb_bits, ctypes.byref(t)), "gf2x_tune_get")
+    return t.as_dict()
+
+
+def gf2x_tune_set(na_bits, nb_bits, fft_depth, fft_buffers, bcvt_tile_log, bcvt_threads, ms=-1.0):
+    t = gf2x_tune_t(int(fft_depth), int(fft_buffers), int(bcvt_tile_log), int(bcvt_threads),
+                    float(ms))
+    _check(load().gf2x_tune_set(na_bits, nb_bits, ctypes.byref(t)), "gf2x_tune_set")
+
+
+def gf2x_tune_save(path):
+    _check(load().gf2x_tune_save(os.fsencode(path)), "gf2x_tune_save")
+
+
+def gf2x_tune_load(path):
+    _check(load().gf2x_tune_load(os.fsencode(path)), "gf2x_tune_load")
 
 
 def gf2x_plan_create(na_bits, nb_bits):

@@ -1,6 +1,6 @@
 """Multiply two seeded random operands on cuda:0 and print the time per product.
 
-    python -m paper_1708_09746_gb300 --log-bits 28 --reps 2
+    python -m paper_1708_09746_gb300 --log-bits 28 --reps 2 [--plan 7 2 11 256]
 
 Each operand has 2^log_bits bits (top bit set, uniform otherwise, seed 1).  The
 first product is a warm-up (it builds the plan and the tables); the command
@@ -23,6 +23,10 @@ def main():
     p.add_argument("--log-bits-b", type=int, default=None,
                    help="log2 of b's length (default: the same as a)")
     p.add_argument("--reps", type=int, default=2)
+    p.add_argument("--plan", type=int, nargs=4, metavar=("DEPTH", "BUFFERS", "TILE_LOG", "THREADS"),
+                   help="plan parameters of the shape (gf2x_tune_set) instead of the defaults")
+    p.add_argument("--autotune", action="store_true",
+                   help="run gf2x_autotune for the shape first and print its choice")
     args = p.parse_args()
     _build.build()
     import paper_1708_09746_gb300 as G
@@ -34,6 +38,10 @@ def main():
     da = torch.from_numpy(a.view(np.int64)).cuda()
     db = torch.from_numpy(b.view(np.int64)).cuda()
     out = torch.empty(G.gf2x_out_words(na, nb), dtype=torch.int64, device="cuda")
+    if args.plan:
+        G.gf2x_tune_set(na, nb, *args.plan)
+    if args.autotune:
+        print("autotune:", G.gf2x_autotune(na, nb))
     torch.cuda.synchronize()
     for i in range(args.reps):
         t0 = time.perf_counter()

@@ -1,6 +1,7 @@
 // The C ABI (include/gf2x_gb300.h): argument checks, per-device tables,
 // plans and the order of the stages of Alg. 5.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -228,8 +229,65 @@ struct StageTimer : StageHook {
 // ---- Plans ------------------------------------------------------------------
 namespace {
 
-int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits) {
-    int rc = gf2x::plan_init(p, na_bits, nb_bits, nullptr);
+// ---- Tuning table: shape (log2 N, log2 Pa, log2 Pb) -> plan parameters ------
+struct TuneEntry {
+    PlanTune t;
+    double ms = -1;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, TuneEntry> g_tune;
+
+std::tuple<int, int, int> shape_key(uint64_t na_bits, uint64_t nb_bits) {
+    int M, pa, pb;
+    shape_of(na_bits, nb_bits, &M, &pa, &pb);
+    return std::make_tuple(M, pa, pb);
+}
+
+TuneEntry tune_for(uint64_t na_bits, uint64_t nb_bits) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(shape_key(na_bits, nb_bits));
+    return it == g_tune.end() ? TuneEntry() : it->second;
+}
+
+bool tune_valid(const gf2x_tune_t &t) {
+    return t.fft_depth >= 1 && t.fft_depth <= kFftGlobalMax && (t.fft_buffers == 1 || t.fft_buffers == 2) &&
+           t.bcvt_tile_log >= 4 &&
+           t.bcvt_tile_log <= 14 && t.bcvt_threads >= 32 && t.bcvt_threads <= 512 &&
+           t.bcvt_threads % 32 == 0;
+}
+
+PlanTune from_abi(const gf2x_tune_t &t) {
+    PlanTune p;
+    p.fft_depth = t.fft_depth;
+    p.fft_nbuf = t.fft_buffers;
+    p.bcvt.tile_min_log = t.bcvt_tile_log;
+    p.bcvt.small_threads = t.bcvt_threads;
+    return p;
+}
+
+gf2x_tune_t to_abi(const TuneEntry &e) {
+    gf2x_tune_t t;
+    t.fft_depth = e.t.fft_depth;
+    t.fft_buffers = e.t.fft_nbuf;
+    t.bcvt_tile_log = e.t.bcvt.tile_min_log;
+    t.bcvt_threads = e.t.bcvt.small_threads;
+    t.ms = e.ms;
+    return t;
+}
+
+void drop_cached_plans_of(const std::tuple<int, int, int> &key);
+
+void tune_store(const std::tuple<int, int, int> &key, const TuneEntry &e) {
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = e;
+    }
+    drop_cached_plans_of(key);
+}
+
+int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits, const PlanTune *tune = nullptr) {
+    const PlanTune t = tune ? *tune : tune_for(na_bits, nb_bits).t;
+    int rc = gf2x::plan_init(p, na_bits, nb_bits, nullptr, t);
     if (rc == -1) return GF2X_EINVAL;
     if (rc == -2) return GF2X_ENOMEM;
     return rc ? GF2X_ECUDA : GF2X_OK;
@@ -249,6 +307,16 @@ int plan_run(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t 
 // Plan cache for the one-shot calls, keyed by (device, sizes).
 std::mutex g_cache_mu;
 std::map<std::tuple<int, uint64_t, uint64_t>, std::shared_ptr<gf2x_plan>> g_cache;
+
+void drop_cached_plans_of(const std::tuple<int, int, int> &key) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (auto it = g_cache.begin(); it != g_cache.end();) {
+        if (shape_key(std::get<1>(it->first), std::get<2>(it->first)) == key)
+            it = g_cache.erase(it);
+        else
+            ++it;
+    }
+}
 
 int cached_plan(uint64_t na_bits, uint64_t nb_bits, std::shared_ptr<gf2x_plan> *out) {
     int dev;
@@ -644,6 +712,190 @@ int gf2x_profile_read(int stage, double *ms, uint64_t *launches, uint64_t *calls
 const char *gf2x_profile_stage_name(int stage) {
     if (stage < 0 || stage >= ST_COUNT) return "";
     return kStageNames[stage];
+}
+
+// ---- Autotuning -------------------------------------------------------------
+
+int gf2x_autotune(uint64_t na_bits, uint64_t nb_bits, int reps, gf2x_tune_t *best) {
+    if (!best) return GF2X_EINVAL;
+    try {
+        int rc = check_sizes(na_bits, nb_bits);
+        if (rc) return rc;
+        if (!na_bits || !nb_bits) return GF2X_EINVAL;
+        const DevTables *T;
+        if ((rc = get_tables(&T))) return rc;
+        if (reps <= 0) reps = 3;
+        int M, pa, pb;
+        shape_of(na_bits, nb_bits, &M, &pa, &pb);
+        if (M > kMaxLogN) return GF2X_EINVAL;
+        // scratch operands (the timing does not depend on the bits), output, workspace
+        const size_t ba = 8 * words_of(na_bits), bb = 8 * words_of(nb_bits);
+        const size_t bo = 8 * gf2x_out_words(na_bits, nb_bits);
+        std::unique_ptr<gf2x_plan> probe(new gf2x_plan());
+        if ((rc = plan_init(probe.get(), na_bits, nb_bits))) return rc;
+        char *buf = nullptr;
+        const size_t total = probe->ws_bytes + ((ba + 255) & ~255ull) + ((bb + 255) & ~255ull) + bo;
+        if (cudaMalloc(reinterpret_cast<void **>(&buf), total) != cudaSuccess) {
+            cudaGetLastError();
+            return GF2X_ENOMEM;
+        }
+        uint64_t *da = reinterpret_cast<uint64_t *>(buf + probe->ws_bytes);
+        uint64_t *db = reinterpret_cast<uint64_t *>(buf + probe->ws_bytes + ((ba + 255) & ~255ull));
+        uint64_t *dout = reinterpret_cast<uint64_t *>(buf + probe->ws_bytes + ((ba + 255) & ~255ull) +
+                                                      ((bb + 255) & ~255ull));
+        cudaMemset(da, 0x5a, ba);
+        cudaMemset(db, 0xa5, bb);
+        cudaStream_t s = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        auto trial = [&](const PlanTune &t, double *ms) -> int {
+            std::unique_ptr<gf2x_plan> pl(new gf2x_plan());
+            int r = plan_init(pl.get(), na_bits, nb_bits, &t);
+            if (r) return r;
+            if ((r = plan_run_core(pl.get(), da, db, dout, buf, s, T, device_status(), nullptr)))
+                return GF2X_ECUDA;
+            cudaEventRecord(e0, s);
+            for (int i = 0; i < reps; i++)
+                if (plan_run_core(pl.get(), da, db, dout, buf, s, T, device_status(), nullptr))
+                    return GF2X_ECUDA;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaGetLastError();
+                return GF2X_ECUDA;
+            }
+            float f = 0;
+            cudaEventElapsedTime(&f, e0, e1);
+            *ms = f / reps;
+            return GF2X_OK;
+        };
+        // 1. fusion depth: the depths that give distinct strided-pass counts
+        TuneEntry bestE;
+        bestE.ms = 1e30;
+        int seen[3][8];
+        int nseen = 0;
+        for (int d = kFftGlobalMax; d >= 4 && rc == GF2X_OK; d--) {
+            auto npass = [&](int top) { return top > kFftTileLog ? (top - kFftTileLog + d - 1) / d : 0; };
+            const int sig[3] = {npass(pa), npass(pb), npass(M)};
+            bool dup = false;
+            for (int q = 0; q < nseen; q++)
+                dup = dup || (seen[0][q] == sig[0] && seen[1][q] == sig[1] && seen[2][q] == sig[2]);
+            if (dup) continue;
+            for (int q = 0; q < 3; q++) seen[q][nseen] = sig[q];
+            nseen++;
+            const bool strided = sig[0] + sig[1] + sig[2] > 0;
+            for (int nb = 2; nb >= (strided ? 1 : 2) && rc == GF2X_OK; nb--) {
+                PlanTune t;
+                t.fft_depth = d;
+                t.fft_nbuf = nb;
+                double ms;
+                if ((rc = trial(t, &ms))) break;
+                if (ms < bestE.ms) {
+                    bestE.t = t;
+                    bestE.ms = ms;
+                }
+            }
+        }
+        // 2. BasisCvt tile shape with that depth
+        const int tiles[4] = {10, 11, 12, 13}, threads[3] = {128, 256, 512};
+        for (int i = 0; i < 4 && rc == GF2X_OK; i++)
+            for (int j = 0; j < 3 && rc == GF2X_OK; j++) {
+                PlanTune t = bestE.t;
+                t.bcvt.tile_min_log = tiles[i];
+                t.bcvt.small_threads = threads[j];
+                if (t.bcvt.tile_min_log == bestE.t.bcvt.tile_min_log &&
+                    t.bcvt.small_threads == bestE.t.bcvt.small_threads)
+                    continue;
+                double ms;
+                if ((rc = trial(t, &ms))) break;
+                if (ms < bestE.ms) {
+                    bestE.t = t;
+                    bestE.ms = ms;
+                }
+            }
+        cudaStreamSynchronize(s);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaStreamDestroy(s);
+        cudaFree(buf);
+        const int st = take_device_status();
+        if (rc == GF2X_OK) rc = st;
+        if (rc) return rc;
+        tune_store(shape_key(na_bits, nb_bits), bestE);
+        *best = to_abi(bestE);
+        return GF2X_OK;
+    } catch (const std::bad_alloc &) {
+        return GF2X_ENOMEM;
+    } catch (...) {
+        return GF2X_ECUDA;
+    }
+}
+
+int gf2x_tune_get(uint64_t na_bits, uint64_t nb_bits, gf2x_tune_t *out) {
+    if (!out || !na_bits || !nb_bits || check_sizes(na_bits, nb_bits)) return GF2X_EINVAL;
+    *out = to_abi(tune_for(na_bits, nb_bits));
+    return GF2X_OK;
+}
+
+int gf2x_tune_set(uint64_t na_bits, uint64_t nb_bits, const gf2x_tune_t *t) {
+    if (!t || !na_bits || !nb_bits || check_sizes(na_bits, nb_bits) || !tune_valid(*t))
+        return GF2X_EINVAL;
+    TuneEntry e;
+    e.t = from_abi(*t);
+    e.ms = t->ms;
+    tune_store(shape_key(na_bits, nb_bits), e);
+    return GF2X_OK;
+}
+
+int gf2x_tune_save(const char *path) {
+    if (!path) return GF2X_EINVAL;
+    FILE *f = std::fopen(path, "w");
+    if (!f) return GF2X_EINVAL;
+    std::fprintf(f, "gf2x-tune 1\n");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (const auto &kv : g_tune)
+            std::fprintf(f, "%d %d %d %d %d %d %d %.6f\n", std::get<0>(kv.first),
+                         std::get<1>(kv.first), std::get<2>(kv.first), kv.second.t.fft_depth,
+                         kv.second.t.fft_nbuf, kv.second.t.bcvt.tile_min_log,
+                         kv.second.t.bcvt.small_threads, kv.second.ms);
+    }
+    const bool ok = std::fclose(f) == 0;
+    return ok ? GF2X_OK : GF2X_EINVAL;
+}
+
+int gf2x_tune_load(const char *path) {
+    if (!path) return GF2X_EINVAL;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return GF2X_EINVAL;
+    char magic[16] = {0};
+    int version = 0;
+    if (std::fscanf(f, "%15s %d", magic, &version) != 2 || std::strcmp(magic, "gf2x-tune") != 0 ||
+        version != 1) {
+        std::fclose(f);
+        return GF2X_EINVAL;
+    }
+    std::vector<std::pair<std::tuple<int, int, int>, TuneEntry>> rows;
+    int M, pa, pb;
+    gf2x_tune_t t;
+    int got;
+    while ((got = std::fscanf(f, "%d %d %d %d %d %d %d %lf", &M, &pa, &pb, &t.fft_depth,
+                              &t.fft_buffers, &t.bcvt_tile_log, &t.bcvt_threads, &t.ms)) == 8) {
+        if (M < 1 || M > kMaxLogN || pa < 0 || pa > M || pb < 0 || pb > M || !tune_valid(t)) {
+            std::fclose(f);
+            return GF2X_EINVAL;
+        }
+        TuneEntry e;
+        e.t = from_abi(t);
+        e.ms = t.ms;
+        rows.emplace_back(std::make_tuple(M, pa, pb), e);
+    }
+    const bool clean = got == EOF;
+    std::fclose(f);
+    if (!clean) return GF2X_EINVAL;
+    for (const auto &r : rows) tune_store(r.first, r.second);
+    return GF2X_OK;
 }
 
 int gf2x_shutdown(void) {

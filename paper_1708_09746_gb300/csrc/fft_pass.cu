@@ -161,8 +161,9 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int g = a.g, c = a.c, uf = a.uf, gt = g - uf;
     const uint32_t tile = 1u << (g + c);
+    const int NB = a.nbuf;
     uint4 *const buf0 = reinterpret_cast<uint4 *>(smem);  // buffer b at buf0 + b * tile
-    uint32_t *ctab = reinterpret_cast<uint32_t *>(smem + 32 * (size_t)tile);  // [gt][7][32]
+    uint32_t *ctab = reinterpret_cast<uint32_t *>(smem + 16 * (size_t)tile * NB);  // [gt][7][32]
     uint32_t *stab = ctab + gt * 224;                                         // [gt][4][224]
     uint32_t *cval = stab + gt * 4 * 224;                                     // [32]
     uint32_t *cnext = cval + 32;                                              // [32]
@@ -174,7 +175,9 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     // rows of at least 16 bytes (c >= 1; strided passes have c >= 5)
     const bool gpipe = from_g && !a.needs_mt && c >= 1;
     uint64_t *g64s = reinterpret_cast<uint64_t *>(tail);             // [tile] if gpipe
-    uint8_t *mt = tail + (gpipe ? 8 * (size_t)tile : 0);             // 64 KiB if needed
+    // if gpipe: the changeRepr tables (8 x 256 elements, 32 KiB) after the blocks
+    uint4 *chr_s = reinterpret_cast<uint4 *>(tail + 8 * (size_t)tile);
+    uint8_t *mt = tail + (gpipe ? 8 * (size_t)tile + 32768 : 0);     // 64 KiB if needed
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const TileGeom G{c, a.k_lo, g, 4};
@@ -204,6 +207,10 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         uint4 *dst = reinterpret_cast<uint4 *>(mt);
         for (int i = threadIdx.x; i < 4096; i += blockDim.x) dst[i] = __ldg(src + i);
     }
+    if (gpipe) {
+        const uint4 *src = &a.T->chr_in[0][0];
+        for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) chr_s[i] = __ldg(src + i);
+    }
     if ((int)threadIdx.x < g && blockIdx.x < ntiles)
         cnext[threadIdx.x] = tile_cval(a, blockIdx.x & tmask, threadIdx.x);
     __syncthreads();
@@ -220,7 +227,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     bool aborted = false, prefetched = false;
     uint32_t i = 0;
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, i++) {
-        const int b = i & 1;
+        const int b = NB == 2 ? (i & 1) : 0;
         uint4 *s = buf0 + (b ? tile : 0);
         const uint64_t tn = t + gridDim.x;
         const uint64_t y = t >> tiles_log, tt = t & tmask;  // product, tile
@@ -228,14 +235,14 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         bool ok = true;
         prefetched = false;
         if (pipe) {
-            if (warp == 0 && tn < ntiles) {
+            if (NB == 2 && warp == 0 && tn < ntiles) {
                 bulk_wait_read_all();  // the stores out of buf[b^1] have read it
                 __syncwarp();
                 tile_load_issue(G, a.F + (tn >> tiles_log) * a.strideF, tn & tmask,
                                 buf0 + (b ? 0 : tile), &bar[b ^ 1], lane);
                 prefetched = true;
             }
-            ok = mbar_wait_bounded(&bar[b], (i >> 1) & 1);
+            ok = mbar_wait_bounded(&bar[b], NB == 2 ? (i >> 1) & 1 : i & 1);
         } else {
             if (warp == 0) bulk_wait_read_all();  // the stores out of buf[b] have read it
             if (gpipe) ok = mbar_wait_bounded(&bar[2], i & 1);
@@ -253,7 +260,13 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         if (threadIdx.x < 32) cval[threadIdx.x] = cnext[threadIdx.x];
         const uint64_t base = tile_base(G, tt);
         if (gpipe) {
-            for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) s[q] = chrepr_ldg(a.T, g64s[q]);
+            for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) {
+                const uint64_t w = g64s[q];
+                uint4 acc = make_uint4(0, 0, 0, 0);
+#pragma unroll
+                for (int p = 0; p < 8; p++) acc = xor4(acc, chr_s[p * 256 + ((w >> (8 * p)) & 255)]);
+                s[q] = acc;
+            }
         } else if (from_g) {
             const uint64_t *gy = a.g64 + y * a.strideW;
             for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) {
@@ -303,6 +316,13 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         fence_proxy_async_smem();
         __syncthreads();
         if (warp == 0) tile_store_issue(G, Fy, tt, s, lane);
+        // one buffer: the next tile comes in once this one has been read out
+        if (pipe && NB == 1 && warp == 0 && tn < ntiles) {
+            bulk_wait_read_all();
+            __syncwarp();
+            tile_load_issue(G, a.F + (tn >> tiles_log) * a.strideF, tn & tmask, buf0, &bar[0],
+                            lane);
+        }
     }
     if (aborted) {
         if (threadIdx.x == 0) atomicExch(a.status, -4);  // GF2X_ETIMEOUT
@@ -414,19 +434,20 @@ int cached_pass_tables(int k_lo, int g, int uf, const uint32_t **d_val, const ui
     return 0;
 }
 
-// Shared memory of a pass: two tile buffers, the shuffle tables of the tile's
+// Shared memory of a pass: one or two tile buffers, the shuffle tables of the tile's
 // multipliers and their staged byte slices, the multipliers, four mbarriers,
-// then the staged 64-bit blocks (first pass without product table) and the
-// F~_{2^8} product table if needed.
-size_t pass_smem(int g, int c, int uf, bool needs_mt, bool from_g) {
-    size_t b = (size_t)32 << (g + c);
+// then the staged 64-bit blocks and the changeRepr tables (first pass without
+// product table) and the F~_{2^8} product table if needed.
+size_t pass_smem(int g, int c, int uf, bool needs_mt, bool from_g, int nbuf) {
+    size_t b = ((size_t)16 * nbuf) << (g + c);
     b += (size_t)(g - uf) * 224 * 4 * 5 + 64 * 4 + 4 * 8;
-    if (from_g && !needs_mt && c >= 1) b += (size_t)8 << (g + c);
+    if (from_g && !needs_mt && c >= 1) b += ((size_t)8 << (g + c)) + 32768;
     if (needs_mt) b += 65536;
     return b;
 }
 
-int make_pass(int k_lo, int g, int c, int uf, int mode, int g_f, PassTableFn src, FftPassCfg *p) {
+int make_pass(int k_lo, int g, int c, int uf, int mode, int g_f, PassTableFn src, FftPassCfg *p,
+              int nbuf = 2) {
     // register sub-passes need a warp's 32 lanes inside the column bits and
     // the rows below the sub-pass, so that the lanes share the multiplier
     if (uf < g && c + uf < 5) return -1;
@@ -439,8 +460,10 @@ int make_pass(int k_lo, int g, int c, int uf, int mode, int g_f, PassTableFn src
     p->mode = mode;
     p->g_f = g_f;
     p->needs_mt = (uf > 0) || mode == 2;
-    p->smem = pass_smem(g, c, uf, p->needs_mt, false);
-    p->threads = std::max(32, std::min(512, (1 << (g + c)) / 2));
+    // one buffer only where two CTAs then fit an SM (no product table)
+    p->nbuf = (nbuf == 1 && !p->needs_mt) ? 1 : 2;
+    p->smem = pass_smem(g, c, uf, p->needs_mt, false, p->nbuf);
+    p->threads = std::max(32, std::min(p->nbuf == 1 ? 256 : 512, (1 << (g + c)) / 2));
     return 0;
 }
 
@@ -453,10 +476,13 @@ int push_pass(PassList &out, const FftPassCfg &p) {
 // Strided passes covering layers [lo, hi) from the top down (forward) or
 // bottom up (inverse), at most kFftGlobalMax layers each, balanced; each
 // tile is 2^g rows by 2^(12-g) columns.
-int global_passes(int lo, int hi, bool inverse, PassTableFn src, PassList &out) {
+int global_passes(int lo, int hi, bool inverse, PassTableFn src, PassList &out, int depth,
+                  int nbuf) {
     const int L = hi - lo;
     if (L <= 0) return 0;
-    const int n = (L + kFftGlobalMax - 1) / kFftGlobalMax;
+    depth = std::max(1, std::min(depth, kFftGlobalMax));
+    depth = std::max(depth, (L + PassList::kMax - 1) / PassList::kMax);  // at most kMax passes
+    const int n = (L + depth - 1) / depth;
     if (n > PassList::kMax) return -1;
     int klo[PassList::kMax], gg[PassList::kMax];
     int k = lo;
@@ -468,7 +494,8 @@ int global_passes(int lo, int hi, bool inverse, PassTableFn src, PassList &out) 
     for (int q = 0; q < n; q++) {
         const int i = inverse ? q : n - 1 - q;
         FftPassCfg p;
-        int rc = make_pass(klo[i], gg[i], kFftTileLog - gg[i], 0, inverse ? 1 : 0, gg[i], src, &p);
+        int rc = make_pass(klo[i], gg[i], kFftTileLog - gg[i], 0, inverse ? 1 : 0, gg[i], src, &p,
+                           nbuf);
         if (rc || (rc = push_pass(out, p))) return rc;
     }
     return 0;
@@ -476,9 +503,9 @@ int global_passes(int lo, int hi, bool inverse, PassTableFn src, PassList &out) 
 
 }  // namespace
 
-int plan_fft_forward(int M, int log_p, PassList &out, PassTableFn src) {
+int plan_fft_forward(int M, int log_p, PassList &out, PassTableFn src, int depth, int nbuf) {
     out.n = 0;
-    int rc = global_passes(kFftTileLog, log_p, false, src, out);
+    int rc = global_passes(kFftTileLog, log_p, false, src, out, depth, nbuf);
     if (rc) return rc;
     const int gl = std::min(log_p, kFftTileLog);
     FftPassCfg p;
@@ -487,31 +514,41 @@ int plan_fft_forward(int M, int log_p, PassList &out, PassTableFn src) {
     return push_pass(out, p);
 }
 
-int plan_fft_inverse(int M, PassList &out, PassTableFn src) {
+int plan_fft_inverse(int M, PassList &out, PassTableFn src, int depth, int nbuf) {
     out.n = 0;
     const int gl = std::min(M, kFftTileLog);
     FftPassCfg p;
     int rc = make_pass(0, gl, 0, std::min(5, gl), 1, gl, src, &p);
     if (rc || (rc = push_pass(out, p))) return rc;
-    return global_passes(kFftTileLog, M, true, src, out);
+    return global_passes(kFftTileLog, M, true, src, out, depth, nbuf);
 }
 
 int plan_fft_fused(int M, int log_p, PassList &fwd_global, FftPassCfg &local, PassList &inv_global,
-                   PassTableFn src) {
+                   PassTableFn src, int depth, int nbuf) {
     fwd_global.n = 0;
     inv_global.n = 0;
-    int rc = global_passes(kFftTileLog, log_p, false, src, fwd_global);
+    int rc = global_passes(kFftTileLog, log_p, false, src, fwd_global, depth, nbuf);
     if (rc) return rc;
     const int gl = std::min(M, kFftTileLog);
     const int gf = std::min(log_p, kFftTileLog);
     if ((rc = make_pass(0, gl, 0, std::min(5, gl), 2, gf, src, &local))) return rc;
-    return global_passes(kFftTileLog, M, true, src, inv_global);
+    return global_passes(kFftTileLog, M, true, src, inv_global, depth, nbuf);
 }
 
 void prepare_fft_attributes() {
     ensure_smem_attr(reinterpret_cast<const void *>(k_fft_pass), 227 * 1024);
     ensure_smem_attr(reinterpret_cast<const void *>(k_pointmul_mt), 65536);
     num_sms();
+}
+
+// CTAs of k_fft_pass resident per SM for this block size and shared memory
+// (at least 1): 128 registers per thread of 64 Ki, 228 KiB of shared memory
+// per SM with 1 KiB reserved per CTA.  Computed rather than queried so that it
+// is safe while a stream is being captured.
+static int resident_ctas(int threads, size_t smem) {
+    const int by_regs = 65536 / std::max(1, threads * 128);
+    const int by_smem = (int)(233472 / (smem + 1024));
+    return std::max(1, std::min(by_regs, by_smem));
 }
 
 int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,
@@ -538,9 +575,12 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
     a.count = count;
     a.strideF = strideF;
     a.strideW = strideW;
+    a.nbuf = p.nbuf;
     const uint64_t tiles = ((1ull << M) >> (p.g + p.c)) * (uint64_t)count;
-    const size_t smem = pass_smem(p.g, p.c, p.uf, p.needs_mt, g64 != nullptr);
-    k_fft_pass<<<(unsigned)std::min<uint64_t>(tiles, num_sms()), p.threads, smem, s>>>(a);
+    const size_t smem = pass_smem(p.g, p.c, p.uf, p.needs_mt, g64 != nullptr, p.nbuf);
+    // persistent CTAs: as many as are resident at once
+    const uint64_t ctas = (uint64_t)num_sms() * resident_ctas(p.threads, smem);
+    k_fft_pass<<<(unsigned)std::min<uint64_t>(tiles, ctas), p.threads, smem, s>>>(a);
     return 0;
 }
 

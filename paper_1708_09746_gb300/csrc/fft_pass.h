@@ -21,6 +21,8 @@ struct FftPassCfg {
     const uint32_t *d_shfl;  // their warp-shuffle tables (rows r >= uf)
     size_t smem;
     int threads;
+    int nbuf;      // tile buffers: 2 (one CTA per SM, next tile loaded while
+                   // this one is computed) or 1 (two CTAs per SM take turns)
 };
 
 struct FftPassArgs {
@@ -37,6 +39,7 @@ struct FftPassArgs {
     int *status;  // device status word (a bounded wait that ran out stores GF2X_ETIMEOUT)
     int count;    // products in the launch: product y at F + y * strideF,
     uint64_t strideF, strideW;  // g64 + y * strideW, FA + y * strideF
+    int nbuf;     // tile buffers (1 or 2)
 };
 
 // A fixed-capacity list of passes (no heap allocation).
@@ -65,10 +68,14 @@ void pass_tables_fill(int k_lo, int g, int uf, uint32_t *val, uint32_t *shfl);
 // fan-outs).  Inverse: all M layers.  Fused: forward of the second operand,
 // its bottom pass merged with pointmul and the bottom inverse layers.
 // Return 0 or a negative status.
-int plan_fft_forward(int M, int log_p, PassList &out, PassTableFn src = nullptr);
-int plan_fft_inverse(int M, PassList &out, PassTableFn src = nullptr);
+// `depth` = the most layers one strided pass covers (1 .. kFftGlobalMax);
+// `nbuf` = tile buffers of the strided passes (1 or 2).
+int plan_fft_forward(int M, int log_p, PassList &out, PassTableFn src = nullptr,
+                     int depth = 7, int nbuf = 2);
+int plan_fft_inverse(int M, PassList &out, PassTableFn src = nullptr, int depth = 7,
+                     int nbuf = 2);
 int plan_fft_fused(int M, int log_p, PassList &fwd_global, FftPassCfg &local, PassList &inv_global,
-                   PassTableFn src = nullptr);
+                   PassTableFn src = nullptr, int depth = 7, int nbuf = 2);
 
 // Layers of the contiguous bottom pass and of each strided pass.
 constexpr int kFftTileLog = 12;

@@ -479,35 +479,51 @@ __global__ void k_chrepr(const uint64_t *__restrict__ g, uint64_t pmask, uint4 *
 // changeRepr^-1 and InterleavedCombine (Sec. 2.1): psi(F[j]) is a polynomial
 // of degree < 128 in z; z -> x and y -> x^64 add its high word into the next
 // output word.
-__device__ __forceinline__ uint4 psi(const DevTables *__restrict__ T, uint4 e) {
+__device__ __forceinline__ uint4 psi(const uint4 *__restrict__ tab, uint4 e) {
     uint4 acc = make_uint4(0, 0, 0, 0);
     const uint32_t wv[4] = {e.x, e.y, e.z, e.w};
 #pragma unroll
     for (int q = 0; q < 4; q++)
 #pragma unroll
-        for (int b = 0; b < 4; b++)
-            acc = xor4(acc, __ldg(&T->chr_out[4 * q + b][(wv[q] >> (8 * b)) & 255]));
+        for (int b = 0; b < 4; b++) acc = xor4(acc, tab[(4 * q + b) * 256 + ((wv[q] >> (8 * b)) & 255)]);
     return acc;
 }
 
-__global__ void k_ichrepr_combine(const uint4 *__restrict__ F, uint64_t n, uint64_t stride,
-                                  OutputDesc one, const OutputDesc *__restrict__ many,
-                                  const DevTables *__restrict__ T) {
+// Each element's psi is computed once, with the 8-bit tables (64 KiB) in
+// shared memory: output word j is the low half of psi(F[j]) XOR the high half
+// of psi(F[j-1]), which the previous lane holds (lane 0 recomputes it).  Whole
+// warps walk the words so that every lane takes part in the shuffles.
+__global__ void __launch_bounds__(256) k_ichrepr_combine(const uint4 *__restrict__ F, uint64_t n,
+                                                         uint64_t stride, OutputDesc one,
+                                                         const OutputDesc *__restrict__ many,
+                                                         const DevTables *__restrict__ T) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint4 *tab = reinterpret_cast<uint4 *>(smem_raw);
+    const uint4 *src = &T->chr_out[0][0];
+    for (int i = threadIdx.x; i < 16 * 256; i += blockDim.x) tab[i] = __ldg(src + i);
+    __syncthreads();
     const OutputDesc d = many ? many[blockIdx.y] : one;
     F += blockIdx.y * stride;
-    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < d.words;
-         j += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t v = 0;
-        if (j < n) {
-            uint4 c = psi(T, F[j]);
-            v ^= (uint64_t)c.x | ((uint64_t)c.y << 32);
+    const int lane = threadIdx.x & 31;
+    for (uint64_t j0 = blockIdx.x * (uint64_t)blockDim.x; j0 < d.words;
+         j0 += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t j = j0 + threadIdx.x;
+        uint4 c = make_uint4(0, 0, 0, 0);
+        if (j < n && j < d.words) c = psi(tab, F[j]);
+        uint32_t hz = __shfl_up_sync(0xffffffffu, c.z, 1), hw = __shfl_up_sync(0xffffffffu, c.w, 1);
+        if (lane == 0) {
+            hz = hw = 0;
+            if (j >= 1 && j - 1 < n && j < d.words) {
+                const uint4 p = psi(tab, F[j - 1]);
+                hz = p.z;
+                hw = p.w;
+            }
         }
-        if (j >= 1 && j - 1 < n) {
-            uint4 c = psi(T, F[j - 1]);
-            v ^= (uint64_t)c.z | ((uint64_t)c.w << 32);
+        if (j < d.words) {
+            uint64_t v = ((uint64_t)c.x | ((uint64_t)c.y << 32)) ^ ((uint64_t)hz | ((uint64_t)hw << 32));
+            if (j == d.words - 1) v &= d.mask;
+            d.out[j] = v;
         }
-        if (j == d.words - 1) v &= d.mask;
-        d.out[j] = v;
     }
 }
 
@@ -697,7 +713,7 @@ static void launch_bcvt_class(T *f, int m, const BcvtOp &o, int inverse, cudaStr
 // list `fwd` (the divisions of Alg. 3 in order) before anything is launched.
 template <typename T>
 uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStream_t s, int count,
-                       uint64_t stride) {
+                       uint64_t stride, const BcvtTune &tune) {
     ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<T>),
                      (int)(sizeof(T) << tile_log_for<T>()));
     uint64_t launches = 0;
@@ -778,7 +794,7 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
         }
         // the smallest tile that holds the steps (at least 2^11 elements):
         // small tiles let two CTAs share an SM and overlap their phases
-        const int tmin = std::min(m, 11);
+        const int tmin = std::min(m, std::max(4, std::min(tune.tile_min_log, tile_log_for<T>())));
         int c, lo, w;
         if (ghi + 1 <= budget) {  // contiguous tile
             c = 0;
@@ -797,7 +813,8 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
             lb.op[q - i] = o;
         }
         size_t smem = sizeof(T) << (c + w);
-        int threads = std::max(32, std::min(smem > 65536 ? 512 : 256, 1 << (c + w - 1)));
+        const int small = std::max(32, std::min(512, tune.small_threads));
+        int threads = std::max(32, std::min(smem > 65536 ? 512 : small, 1 << (c + w - 1)));
         dim3 grid((unsigned)(n >> (c + w)), count);
         k_bcvt_tile<T><<<grid, threads, smem, s>>>(f, c, lo, w, lb, inverse, stride);
         launches++;
@@ -811,6 +828,7 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
 }
 
 void prepare_bcvt_attributes() {
+    ensure_smem_attr(reinterpret_cast<const void *>(k_ichrepr_combine), 65536);
     ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint64_t>),
                      (int)(sizeof(uint64_t) << tile_log_for<uint64_t>()));
     ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint4>),
@@ -819,9 +837,9 @@ void prepare_bcvt_attributes() {
 }
 
 template uint64_t run_basis_cvt<uint64_t>(uint64_t *, int, const LevelList &, int, cudaStream_t,
-                                          int, uint64_t);
+                                          int, uint64_t, const BcvtTune &);
 template uint64_t run_basis_cvt<uint4>(uint4 *, int, const LevelList &, int, cudaStream_t, int,
-                                       uint64_t);
+                                       uint64_t, const BcvtTune &);
 
 void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const DevTables *T,
                    cudaStream_t s) {
@@ -831,8 +849,12 @@ void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const De
 void launch_ichrepr_combine(const uint4 *F, uint64_t n, uint64_t stride, const OutputDesc &one,
                             const OutputDesc *many, int count, uint64_t max_words,
                             const DevTables *T, cudaStream_t s) {
-    dim3 grid(grid_for(max_words, 256, count), count);
-    k_ichrepr_combine<<<grid, 256, 0, s>>>(F, n, stride, one, many, T);
+    ensure_smem_attr(reinterpret_cast<const void *>(k_ichrepr_combine), 65536);
+    // a few resident CTAs per SM, each loading the 64 KiB of tables once
+    const uint64_t per = std::max<uint64_t>(1, (uint64_t)num_sms() * 3 / (uint64_t)std::max(count, 1));
+    const uint64_t need = (max_words + 255) / 256;
+    dim3 grid((unsigned)std::max<uint64_t>(1, std::min(need, per)), count);
+    k_ichrepr_combine<<<grid, 256, 65536, s>>>(F, n, stride, one, many, T);
 }
 
 }  // namespace gf2x

@@ -61,9 +61,16 @@ void launch_split_pad(const OperandDesc &one, const OperandDesc *many, int count
 // BasisCvt (inverse = 0) or iBasisCvt (inverse = 1) on 2^m coefficients of
 // type T (uint64_t or uint4), with the forward level list `fwd`, for `count`
 // arrays at f + y * stride.  Returns the number of kernel launches enqueued.
+// Shape of the BasisCvt tile passes: the smallest tile (log2 of its
+// elements) and the threads of a CTA whose tile is at most 64 KiB.
+struct BcvtTune {
+    int tile_min_log = 11;
+    int small_threads = 256;
+};
+
 template <typename T>
 uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStream_t s,
-                       int count = 1, uint64_t stride = 0);
+                       int count = 1, uint64_t stride = 0, const BcvtTune &tune = BcvtTune());
 
 void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const DevTables *T,
                    cudaStream_t s);

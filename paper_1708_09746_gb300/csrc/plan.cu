@@ -28,7 +28,16 @@ void fill_dev_tables(DevTables *h) {
     std::memcpy(h->shfl_m4r, H.shfl_m4r, sizeof(H.shfl_m4r));
 }
 
-int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits, PassTableFn src) {
+void shape_of(uint64_t na_bits, uint64_t nb_bits, int *M, int *pa_log, int *pb_log) {
+    const uint64_t na_w = words_of(na_bits), nb_w = words_of(nb_bits);
+    *M = log2_ceil(std::max<uint64_t>(2, na_w + nb_w - 1));
+    *pa_log = log2_ceil(na_w);
+    *pb_log = log2_ceil(nb_w);
+}
+
+int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits, PassTableFn src,
+              const PlanTune &tune) {
+    p->tune = tune;
     p->na_bits = na_bits;
     p->nb_bits = nb_bits;
     p->na_w = words_of(na_bits);
@@ -48,9 +57,11 @@ int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits, PassTableFn src)
     p->lv_a = basis_cvt_levels(p->pa_log);
     p->lv_b = basis_cvt_levels(p->pb_log);
     p->lv_c = basis_cvt_levels(p->M);
-    int rc = plan_fft_forward(p->M, p->pa_log, p->fft_a, src);
+    int rc = plan_fft_forward(p->M, p->pa_log, p->fft_a, src, tune.fft_depth, tune.fft_nbuf);
     if (rc) return rc;
-    if ((rc = plan_fft_fused(p->M, p->pb_log, p->fft_b, p->fused, p->ifft_top, src))) return rc;
+    if ((rc = plan_fft_fused(p->M, p->pb_log, p->fft_b, p->fused, p->ifft_top, src,
+                             tune.fft_depth, tune.fft_nbuf)))
+        return rc;
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     p->off_fa = 0;
     p->off_fb = up(p->off_fa + 16 * p->N);
@@ -88,7 +99,7 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
     launch_split_pad(one_a, many_a, count, WA, p->Pa, sW, s);
     end(1);
     begin(ST_BCVT);
-    end(run_basis_cvt<uint64_t>(WA, p->pa_log, p->lv_a, 0, s, count, sW));
+    end(run_basis_cvt<uint64_t>(WA, p->pa_log, p->lv_a, 0, s, count, sW, p->tune.bcvt));
     begin(ST_FFT_A);
     for (int i = 0; i < p->fft_a.n; i++)
         launch_fft_pass(p->fft_a.v[i], p->M, FA, i == 0 ? WA : nullptr, p->Pa, nullptr, T, st, s,
@@ -100,7 +111,7 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
     launch_split_pad(one_b, many_b, count, WB, p->Pb, sW, s);
     end(1);
     begin(ST_BCVT);
-    end(run_basis_cvt<uint64_t>(WB, p->pb_log, p->lv_b, 0, s, count, sW));
+    end(run_basis_cvt<uint64_t>(WB, p->pb_log, p->lv_b, 0, s, count, sW, p->tune.bcvt));
     begin(ST_FFT_B);
     for (int i = 0; i < p->fft_b.n; i++)
         launch_fft_pass(p->fft_b.v[i], p->M, FB, i == 0 ? WB : nullptr, p->Pb, nullptr, T, st, s,
@@ -118,7 +129,7 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
     end(p->ifft_top.n);
     // iBasisCvt
     begin(ST_IBCVT);
-    end(run_basis_cvt<uint4>(FB, p->M, p->lv_c, 1, s, count, sF));
+    end(run_basis_cvt<uint4>(FB, p->M, p->lv_c, 1, s, count, sF, p->tune.bcvt));
     // changeRepr^-1 + InterleavedCombine
     begin(ST_OUT);
     launch_ichrepr_combine(FB, p->N, sF, one_out, many_out, count,

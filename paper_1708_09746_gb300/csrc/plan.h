@@ -12,8 +12,21 @@
 #include "gf2x_internal.h"
 #include "kernels.h"
 
+namespace gf2x {
+// Shape parameters of a plan that do not change its results: the FFT fusion
+// depth (most layers per strided pass), the strided passes' tile buffering
+// and the BasisCvt tile shape.  The
+// autotuner (gf2x_autotune) picks them per product shape.
+struct PlanTune {
+    int fft_depth = 7;
+    int fft_nbuf = 2;  // tile buffers of the strided FFT passes (1 or 2)
+    BcvtTune bcvt;
+};
+}  // namespace gf2x
+
 struct gf2x_plan {
     uint64_t na_bits, nb_bits, na_w, nb_w, out_words, total_bits;
+    gf2x::PlanTune tune;
     int M, pa_log, pb_log;
     uint64_t N, Pa, Pb;
     gf2x::LevelList lv_a, lv_b, lv_c;
@@ -51,7 +64,12 @@ inline int log2_ceil(uint64_t n) {
 
 // Fills *p for operands of na_bits and nb_bits (both > 0).  `src` supplies the
 // per-pass device tables (nullptr: the library's cache).  Returns a status.
-int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits, PassTableFn src);
+int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits, PassTableFn src,
+              const PlanTune &tune = PlanTune());
+
+// The shape key of a product: (log2 N, log2 Pa, log2 Pb); products with the
+// same key share their plan structure and their tuned parameters.
+void shape_of(uint64_t na_bits, uint64_t nb_bits, int *M, int *pa_log, int *pb_log);
 
 // Enqueues the whole product on `s` with workspace `ws` (p->ws_bytes bytes,
 // 256-byte aligned), tables T and status word `status`; `hook` may be null.
