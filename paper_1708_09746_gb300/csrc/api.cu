@@ -295,12 +295,12 @@ int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits, const PlanTune *
 
 // Alg. 5, stage after stage, on `s`, with the library's tables.
 int plan_run(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out, void *ws,
-             cudaStream_t s, cudaEvent_t b_ready = nullptr) {
+             cudaStream_t s, cudaEvent_t b_ready = nullptr, const OutputDrain *drain = nullptr) {
     const DevTables *T;
     int rc = get_tables(&T);
     if (rc) return rc;
     StageTimer tm(s);
-    rc = plan_run_core(p, a, b, out, ws, s, T, device_status(), &tm, b_ready);
+    rc = plan_run_core(p, a, b, out, ws, s, T, device_status(), &tm, b_ready, drain);
     return rc ? GF2X_ECUDA : GF2X_OK;
 }
 
@@ -466,25 +466,33 @@ int gf2x_mul_host(const uint64_t *a_host, uint64_t na_bits, const uint64_t *b_ho
                                                       ((bb + 255) & ~255ull));
         // b is uploaded on the copy stream while a is split, converted and
         // transformed on s; the product path waits for it before Split(b).
-        cudaEvent_t alloc_done = nullptr, b_ready = nullptr;
-        if (cudaEventCreateWithFlags(&alloc_done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b_ready, cudaEventDisableTiming) != cudaSuccess) {
+        // The output is written in pieces, each copied back on the copy
+        // stream while the next one is computed.
+        constexpr int kPieces = 4;
+        cudaEvent_t ev[kPieces + 3] = {};
+        bool ev_ok = true;
+        for (auto &e : ev) ev_ok = ev_ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (!ev_ok) {
             cudaGetLastError();
-            if (alloc_done) cudaEventDestroy(alloc_done);
+            for (auto &e : ev)
+                if (e) cudaEventDestroy(e);
             ws_free(buf, s);
             return GF2X_ECUDA;
         }
-        cudaEventRecord(alloc_done, s);
+        cudaEvent_t alloc_done = ev[kPieces], b_ready = ev[kPieces + 1], drained = ev[kPieces + 2];
+        // a first, alone on the link; b after it, while a is being processed
         cudaMemcpyAsync(da, a_host, ba, cudaMemcpyHostToDevice, s);
+        cudaEventRecord(alloc_done, s);
         cudaStreamWaitEvent(cs, alloc_done, 0);
         cudaMemcpyAsync(db, b_host, bb, cudaMemcpyHostToDevice, cs);
         cudaEventRecord(b_ready, cs);
-        rc = plan_run(p.get(), da, db, dout, buf, s, b_ready);
-        cudaMemcpyAsync(out_host, dout, bo, cudaMemcpyDeviceToHost, s);
+        const OutputDrain drain{cs, out_host, kPieces, ev};
+        rc = plan_run(p.get(), da, db, dout, buf, s, b_ready, &drain);
+        cudaEventRecord(drained, cs);
+        cudaStreamWaitEvent(s, drained, 0);  // the copies have read the buffer
         ws_free(buf, s);
         cudaError_t e = cudaStreamSynchronize(s);
-        cudaEventDestroy(alloc_done);
-        cudaEventDestroy(b_ready);
+        for (auto &x : ev) cudaEventDestroy(x);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return GF2X_ECUDA;

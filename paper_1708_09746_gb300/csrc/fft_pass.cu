@@ -578,9 +578,13 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
     a.nbuf = p.nbuf;
     const uint64_t tiles = ((1ull << M) >> (p.g + p.c)) * (uint64_t)count;
     const size_t smem = pass_smem(p.g, p.c, p.uf, p.needs_mt, g64 != nullptr, p.nbuf);
-    // persistent CTAs: as many as are resident at once
-    const uint64_t ctas = (uint64_t)num_sms() * resident_ctas(p.threads, smem);
-    k_fft_pass<<<(unsigned)std::min<uint64_t>(tiles, ctas), p.threads, smem, s>>>(a);
+    // persistent CTAs: as many as are resident at once; a CTA alone on its SM
+    // (shared memory too large for two) gets the full 512 threads
+    int threads = p.threads;
+    int per_sm = resident_ctas(threads, smem);
+    if (per_sm == 1) threads = std::max(threads, std::min(512, (1 << (p.g + p.c)) / 2));
+    const uint64_t ctas = (uint64_t)num_sms() * per_sm;
+    k_fft_pass<<<(unsigned)std::min<uint64_t>(tiles, ctas), threads, smem, s>>>(a);
     return 0;
 }
 

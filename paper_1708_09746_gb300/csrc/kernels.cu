@@ -87,6 +87,13 @@ __global__ void k_bcvt_level(T *f, uint64_t n_half, int logE, int loge, int inve
 // thread loads one class into registers, applies the G divisions with the
 // exact step conditions of each row's position, and stores it back: one
 // shared-memory round trip per run instead of one per level.
+// Shared-memory position of tile index x: the low four bits are XORed with
+// bits 4..7, so that threads reading groups of 16 consecutive elements at the
+// same offset hit different banks (a bijection on every aligned 256-element
+// block; runs of consecutive indices stay consecutive up to a permutation
+// inside each aligned 16-element block).
+__device__ __forceinline__ uint32_t sw(uint32_t x) { return x ^ ((x >> 4) & 15u); }
+
 template <typename T, int G, int RM, bool INV>
 __device__ __forceinline__ void bcvt_run(T *s, uint32_t tile, int a_top, int K) {
     const int a_low = a_top - G + 1;
@@ -101,18 +108,18 @@ __device__ __forceinline__ void bcvt_run(T *s, uint32_t tile, int a_top, int K) 
     const uint32_t r_int = (1u << G) << (a_low - K);
     for (uint32_t q = threadIdx.x; q < items; q += blockDim.x) {
         const uint32_t seg = q / S, r = q - seg * S;
-        T *const sb = s + seg * Z + r;
+        const uint32_t sb = seg * Z + r;
         if (r >= r_int) {
             T v[1 << G];
 #pragma unroll
-            for (int n = 0; n < (1 << G); n++) v[n] = sb[n * S];
+            for (int n = 0; n < (1 << G); n++) v[n] = s[sw(sb + n * S)];
 #pragma unroll
             for (int jj = 0; jj < G; jj++)
 #pragma unroll
                 for (int n = 0; n < (1 << G); n++)
                     if (!((n >> jj) & 1)) v[n] = xr(v[n], v[n + (1 << jj)]);
 #pragma unroll
-            for (int n = 0; n < (1 << G); n++) sb[n * S] = v[n];
+            for (int n = 0; n < (1 << G); n++) s[sw(sb + n * S)] = v[n];
             continue;
         }
         T v[RM];
@@ -121,7 +128,7 @@ __device__ __forceinline__ void bcvt_run(T *s, uint32_t tile, int a_top, int K) 
         for (int n = 0; n < RM; n++) {
             if (r + (uint32_t)n * S < Z) {
                 valid |= 1u << n;
-                v[n] = sb[n * S];
+                v[n] = s[sw(sb + n * S)];
             } else {
                 memset(&v[n], 0, sizeof(T));
             }
@@ -146,7 +153,7 @@ __device__ __forceinline__ void bcvt_run(T *s, uint32_t tile, int a_top, int K) 
         }
 #pragma unroll
         for (int n = 0; n < RM; n++)
-            if ((valid >> n) & 1u) sb[n * S] = v[n];
+            if ((valid >> n) & 1u) s[sw(sb + n * S)] = v[n];
     }
 }
 
@@ -274,10 +281,10 @@ __device__ __forceinline__ void bcvt_sub(T *s, uint32_t tile, int sc) {
     constexpr int N = 1 << M;
     const uint32_t groups = tile >> M, lowmask = (1u << sc) - 1;
     for (uint32_t q = threadIdx.x; q < groups; q += blockDim.x) {
-        T *const sb = s + (((q >> sc) << (sc + M)) | (q & lowmask));
+        const uint32_t sb = ((q >> sc) << (sc + M)) | (q & lowmask);
         T v[N];
 #pragma unroll
-        for (int i = 0; i < N; i++) v[i] = sb[i << sc];
+        for (int i = 0; i < N; i++) v[i] = s[sw(sb + (i << sc))];
         if constexpr (M == 2) {
             div_regs<4, 2, 1, INV>(v);
         } else if constexpr (!INV) {
@@ -292,7 +299,7 @@ __device__ __forceinline__ void bcvt_sub(T *s, uint32_t tile, int sc) {
             div_regs<16, 8, 2, true>(v);
         }
 #pragma unroll
-        for (int i = 0; i < N; i++) sb[i << sc] = v[i];
+        for (int i = 0; i < N; i++) s[sw(sb + (i << sc))] = v[i];
     }
 }
 
@@ -335,7 +342,7 @@ __global__ void __launch_bounds__(512, 1) k_bcvt_tile(T *f, int c, int lo, int w
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const uint32_t i = i0 + u * blockDim.x;
-            if (i < tile) s[i] = v[u];
+            if (i < tile) s[sw(i)] = v[u];
         }
     }
     __syncthreads();
@@ -347,7 +354,7 @@ __global__ void __launch_bounds__(512, 1) k_bcvt_tile(T *f, int c, int lo, int w
         __syncthreads();
     }
     for (uint32_t i = threadIdx.x; i < tile; i += blockDim.x)
-        f[base | ((uint64_t)(i >> c) << lo) | (i & cmask)] = s[i];
+        f[base | ((uint64_t)(i >> c) << lo) | (i & cmask)] = s[sw(i)];
 }
 
 // ---------------------------------------------------------------------------
@@ -496,7 +503,8 @@ __device__ __forceinline__ uint4 psi(const uint4 *__restrict__ tab, uint4 e) {
 __global__ void __launch_bounds__(256) k_ichrepr_combine(const uint4 *__restrict__ F, uint64_t n,
                                                          uint64_t stride, OutputDesc one,
                                                          const OutputDesc *__restrict__ many,
-                                                         const DevTables *__restrict__ T) {
+                                                         const DevTables *__restrict__ T,
+                                                         uint64_t j_begin, uint64_t j_end) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint4 *tab = reinterpret_cast<uint4 *>(smem_raw);
     const uint4 *src = &T->chr_out[0][0];
@@ -505,21 +513,22 @@ __global__ void __launch_bounds__(256) k_ichrepr_combine(const uint4 *__restrict
     const OutputDesc d = many ? many[blockIdx.y] : one;
     F += blockIdx.y * stride;
     const int lane = threadIdx.x & 31;
-    for (uint64_t j0 = blockIdx.x * (uint64_t)blockDim.x; j0 < d.words;
+    const uint64_t j_stop = j_end < d.words ? j_end : d.words;  // words [j_begin, j_stop)
+    for (uint64_t j0 = j_begin + blockIdx.x * (uint64_t)blockDim.x; j0 < j_stop;
          j0 += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t j = j0 + threadIdx.x;
         uint4 c = make_uint4(0, 0, 0, 0);
-        if (j < n && j < d.words) c = psi(tab, F[j]);
+        if (j < n && j < j_stop) c = psi(tab, F[j]);
         uint32_t hz = __shfl_up_sync(0xffffffffu, c.z, 1), hw = __shfl_up_sync(0xffffffffu, c.w, 1);
         if (lane == 0) {
             hz = hw = 0;
-            if (j >= 1 && j - 1 < n && j < d.words) {
+            if (j >= 1 && j - 1 < n && j < j_stop) {
                 const uint4 p = psi(tab, F[j - 1]);
                 hz = p.z;
                 hw = p.w;
             }
         }
-        if (j < d.words) {
+        if (j < j_stop) {
             uint64_t v = ((uint64_t)c.x | ((uint64_t)c.y << 32)) ^ ((uint64_t)hz | ((uint64_t)hw << 32));
             if (j == d.words - 1) v &= d.mask;
             d.out[j] = v;
@@ -848,13 +857,15 @@ void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const De
 
 void launch_ichrepr_combine(const uint4 *F, uint64_t n, uint64_t stride, const OutputDesc &one,
                             const OutputDesc *many, int count, uint64_t max_words,
-                            const DevTables *T, cudaStream_t s) {
+                            const DevTables *T, cudaStream_t s, uint64_t j_begin,
+                            uint64_t j_end) {
     ensure_smem_attr(reinterpret_cast<const void *>(k_ichrepr_combine), 65536);
     // a few resident CTAs per SM, each loading the 64 KiB of tables once
     const uint64_t per = std::max<uint64_t>(1, (uint64_t)num_sms() * 3 / (uint64_t)std::max(count, 1));
-    const uint64_t need = (max_words + 255) / 256;
+    const uint64_t span = std::min(j_end, max_words) > j_begin ? std::min(j_end, max_words) - j_begin : 0;
+    const uint64_t need = (span + 255) / 256;
     dim3 grid((unsigned)std::max<uint64_t>(1, std::min(need, per)), count);
-    k_ichrepr_combine<<<grid, 256, 65536, s>>>(F, n, stride, one, many, T);
+    k_ichrepr_combine<<<grid, 256, 65536, s>>>(F, n, stride, one, many, T, j_begin, j_end);
 }
 
 }  // namespace gf2x

@@ -77,9 +77,10 @@ void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const De
 
 // changeRepr^-1 + InterleavedCombine of `count` products: product y reads n
 // elements at F + y * stride and writes many[y] (or `one`); max_words bounds
-// the output lengths.
+// the output lengths.  Only output words [j_begin, j_end) are written.
 void launch_ichrepr_combine(const uint4 *F, uint64_t n, uint64_t stride, const OutputDesc &one,
                             const OutputDesc *many, int count, uint64_t max_words,
-                            const DevTables *T, cudaStream_t s);
+                            const DevTables *T, cudaStream_t s, uint64_t j_begin = 0,
+                            uint64_t j_end = ~0ull);
 
 }  // namespace gf2x

@@ -79,7 +79,7 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
                    const OperandDesc *many_b, const OutputDesc *many_out, const OperandDesc &one_a,
                    const OperandDesc &one_b, const OutputDesc &one_out, uint64_t max_out_words,
                    void *ws, size_t ws_stride, cudaStream_t s, const DevTables *T, int *st,
-                   StageHook *hook, cudaEvent_t b_ready) {
+                   StageHook *hook, cudaEvent_t b_ready, const OutputDrain *drain) {
     char *base = static_cast<char *>(ws);
     uint4 *FA = reinterpret_cast<uint4 *>(base + p->off_fa);
     uint4 *FB = reinterpret_cast<uint4 *>(base + p->off_fb);
@@ -132,9 +132,23 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
     end(run_basis_cvt<uint4>(FB, p->M, p->lv_c, 1, s, count, sF, p->tune.bcvt));
     // changeRepr^-1 + InterleavedCombine
     begin(ST_OUT);
-    launch_ichrepr_combine(FB, p->N, sF, one_out, many_out, count,
-                           many_out ? max_out_words : one_out.words, T, s);
-    end(1);
+    if (drain && count == 1 && !many_out && drain->chunks > 1) {
+        const uint64_t words = one_out.words, piece = (words + drain->chunks - 1) / drain->chunks;
+        for (int c = 0; c < drain->chunks; c++) {
+            const uint64_t j0 = std::min(words, c * piece), j1 = std::min(words, j0 + piece);
+            launch_ichrepr_combine(FB, p->N, sF, one_out, nullptr, 1, words, T, s, j0, j1);
+            cudaEventRecord(drain->events[c], s);
+            cudaStreamWaitEvent(drain->stream, drain->events[c], 0);
+            if (j1 > j0)
+                cudaMemcpyAsync(drain->host + j0, one_out.out + j0, (j1 - j0) * 8,
+                                cudaMemcpyDeviceToHost, drain->stream);
+        }
+        end(drain->chunks);
+    } else {
+        launch_ichrepr_combine(FB, p->N, sF, one_out, many_out, count,
+                               many_out ? max_out_words : one_out.words, T, s);
+        end(1);
+    }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? 0 : -3;
 }
@@ -143,12 +157,12 @@ uint64_t mask_of_bits(uint64_t bits) { return (bits % 64) ? ((1ull << (bits % 64
 
 int plan_run_core(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out,
                   void *ws, cudaStream_t s, const DevTables *T, int *st, StageHook *hook,
-                  cudaEvent_t b_ready) {
+                  cudaEvent_t b_ready, const OutputDrain *drain) {
     const OperandDesc da{a, p->na_w, mask_of_bits(p->na_bits)};
     const OperandDesc db{b, p->nb_w, mask_of_bits(p->nb_bits)};
     const OutputDesc dout{out, p->out_words, mask_of_bits(p->total_bits)};
     return plan_run_batch(p, 1, nullptr, nullptr, nullptr, da, db, dout, p->out_words, ws,
-                          p->ws_bytes, s, T, st, hook, b_ready);
+                          p->ws_bytes, s, T, st, hook, b_ready, drain);
 }
 
 }  // namespace gf2x

@@ -75,9 +75,18 @@ void shape_of(uint64_t na_bits, uint64_t nb_bits, int *M, int *pa_log, int *pb_l
 // 256-byte aligned), tables T and status word `status`; `hook` may be null.
 // If b_ready is given, the stages of b start after it (b may still be
 // arriving while a is split, converted and transformed).
+// If `drain` is given (one product), the output is produced in drain->chunks
+// pieces and each piece is copied to drain->host on drain->stream as soon as
+// it is written (the copies overlap the rest of the output stage).
+struct OutputDrain {
+    cudaStream_t stream;
+    uint64_t *host;
+    int chunks;
+    cudaEvent_t *events;  // `chunks` events, owned by the caller
+};
 int plan_run_core(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out,
                   void *ws, cudaStream_t s, const DevTables *T, int *status, StageHook *hook,
-                  cudaEvent_t b_ready = nullptr);
+                  cudaEvent_t b_ready = nullptr, const OutputDrain *drain = nullptr);
 
 // `count` products sharing plan p (same M, log2 Pa, log2 Pb): product y's
 // operands and output from many_a[y], many_b[y], many_out[y] (device arrays;
@@ -87,7 +96,8 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
                    const OperandDesc *many_b, const OutputDesc *many_out, const OperandDesc &one_a,
                    const OperandDesc &one_b, const OutputDesc &one_out, uint64_t max_out_words,
                    void *ws, size_t ws_stride, cudaStream_t s, const DevTables *T, int *status,
-                   StageHook *hook, cudaEvent_t b_ready = nullptr);
+                   StageHook *hook, cudaEvent_t b_ready = nullptr,
+                   const OutputDrain *drain = nullptr);
 
 uint64_t mask_of_bits(uint64_t bits);
 

@@ -115,6 +115,21 @@ def test_plan_api_and_host_api():
     assert np.array_equal(host_out, want)
 
 
+@pytest.mark.parametrize("na,nb", [(1, 1), (64, 64), (65, 64), (129, 70), (190, 3),
+                                   (1000, 777), (64 * 37 + 5, 64 * 11), (1 << 18, (1 << 18) - 3)])
+def test_host_buffers_pieces(na, nb):
+    # gf2x_mul_host writes its output in four pieces, each copied back while
+    # the next is computed: outputs of 1 .. 3 words leave pieces empty
+    a, b = W.operand_pair(na * 7 + nb, na, nb)
+    want = P.mul(a, na, b, nb)
+    host_out = np.full(len(want) + 2, 0xA5A5A5A5A5A5A5A5, dtype=np.uint64)
+    pinned = torch.from_numpy(host_out.view(np.int64)).pin_memory()
+    G.gf2x_mul_host(a, na, b, nb, pinned)
+    got = pinned.numpy().view(np.uint64)
+    assert np.array_equal(got[:len(want)], want)
+    assert all(int(x) == 0xA5A5A5A5A5A5A5A5 for x in got[len(want):])
+
+
 def test_batched_uneven():
     lens = W.log_uniform_lengths(7, 24, 6, 16)
     pairs = []
