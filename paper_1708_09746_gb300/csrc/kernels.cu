@@ -318,8 +318,11 @@ __device__ __forceinline__ void bcvt_op(T *s, uint32_t tile, const BcvtOp &op) {
 // bits [loge, logE] lie inside the rows acts on the tile-local index
 // (row << c) | col exactly as on the global index, with logE and loge moved
 // by c - lo (the steps in `lb` are given in tile-local form).
-template <typename T>
-__global__ void __launch_bounds__(512, 1) k_bcvt_tile(T *f, int c, int lo, int w, LevelBatch lb,
+// SMALL: launched with at most 256 threads and 64 KiB of shared memory; for
+// 64-bit coefficients four such CTAs share an SM (64 registers per thread).
+template <typename T, bool SMALL>
+__global__ void __launch_bounds__(SMALL ? 256 : 512, (SMALL && sizeof(T) == 8) ? 4 : 1)
+    k_bcvt_tile(T *f, int c, int lo, int w, LevelBatch lb,
                                                       int inverse, uint64_t stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s = reinterpret_cast<T *>(smem_raw);
@@ -723,8 +726,9 @@ static void launch_bcvt_class(T *f, int m, const BcvtOp &o, int inverse, cudaStr
 template <typename T>
 uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStream_t s, int count,
                        uint64_t stride, const BcvtTune &tune) {
-    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<T>),
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<T, false>),
                      (int)(sizeof(T) << tile_log_for<T>()));
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<T, true>), 65536);
     uint64_t launches = 0;
     const int h_top = top_levels(m, fwd);
     const int budget = std::min(tile_log_for<T>(), m), cmin = min_cols_for<T>();
@@ -825,7 +829,10 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
         const int small = std::max(32, std::min(512, tune.small_threads));
         int threads = std::max(32, std::min(smem > 65536 ? 512 : small, 1 << (c + w - 1)));
         dim3 grid((unsigned)(n >> (c + w)), count);
-        k_bcvt_tile<T><<<grid, threads, smem, s>>>(f, c, lo, w, lb, inverse, stride);
+        if (threads <= 256 && smem <= 65536)
+            k_bcvt_tile<T, true><<<grid, threads, smem, s>>>(f, c, lo, w, lb, inverse, stride);
+        else
+            k_bcvt_tile<T, false><<<grid, threads, smem, s>>>(f, c, lo, w, lb, inverse, stride);
         launches++;
         i = j;
     }
@@ -838,10 +845,12 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
 
 void prepare_bcvt_attributes() {
     ensure_smem_attr(reinterpret_cast<const void *>(k_ichrepr_combine), 65536);
-    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint64_t>),
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint64_t, false>),
                      (int)(sizeof(uint64_t) << tile_log_for<uint64_t>()));
-    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint4>),
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint4, false>),
                      (int)(sizeof(uint4) << tile_log_for<uint4>()));
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint64_t, true>), 65536);
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint4, true>), 65536);
     num_sms();
 }
 
