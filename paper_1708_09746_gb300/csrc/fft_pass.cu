@@ -97,6 +97,59 @@ __device__ __forceinline__ void run_subpass(int G, uint4 *s, int c, int g, int r
     }
 }
 
+// Layers 3 .. 3+NR-1 of a contiguous tile (c = 0), NR = 1 or 2, with
+// warp-uniform multipliers: a thread holds ONE 32-bit limb of the elements
+// that differ in index bits 3 .. 2+NR of a group of 2^(3+NR) elements, and the
+// 32 lanes of a warp are the 4 limbs x 8 elements (bits 0..2) of that group.
+// All lanes then share the group's multipliers, so the shuffle tables apply
+// here although a butterfly block of these layers is smaller than a warp of
+// whole elements (Prop. 3.2: the limbs are multiplied independently).  Lane l
+// reads word (element << 2) + (l & 3) of element base + (l >> 2): one
+// conflict-free 128-byte row per value.
+template <int NR, bool INV>
+__device__ __forceinline__ void limb_subpass(uint4 *s, int g, int uf, const uint32_t *ctab,
+                                             const uint32_t *__restrict__ d_shfl) {
+    uint32_t *wds = reinterpret_cast<uint32_t *>(s);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t groups = 1u << (g - 3 - NR);
+    for (uint32_t grp = warp; grp < groups; grp += nwarps) {
+        uint32_t v[1 << NR];
+#pragma unroll
+        for (int m = 0; m < (1 << NR); m++)
+            v[m] = wds[((((grp << NR) | (uint32_t)m) << 3) << 2) + lane];
+#pragma unroll
+        for (int step = 0; step < NR; step++) {
+            const int rr = INV ? step : (NR - 1 - step);
+            const int r = 3 + rr;
+            const uint32_t off = (1u << (g - uf)) - (1u << (g - r));
+#pragma unroll
+            for (int B = 0; B < (1 << (NR - 1 - rr)); B++) {
+                const uint32_t prefix = (grp << (NR - 1 - rr)) | (uint32_t)B;
+                ShflTab T;
+                const uint32_t *dp = d_shfl + (size_t)(off + prefix) * 224 + lane;
+                const uint32_t *cp = ctab + (r - uf) * 224 + lane;
+#pragma unroll
+                for (int w = 0; w < 7; w++) T.t[w] = cp[32 * w] ^ __ldg(dp + 32 * w);
+#pragma unroll
+                for (int j = 0; j < (1 << rr); j++) {
+                    uint32_t &u = v[B * (2 << rr) + j];
+                    uint32_t &x = v[B * (2 << rr) + j + (1 << rr)];
+                    if (!INV) {
+                        u ^= shfl_mul32(x, T);
+                        x ^= u;
+                    } else {
+                        x ^= u;
+                        u ^= shfl_mul32(x, T);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < (1 << NR); m++)
+            wds[((((grp << NR) | (uint32_t)m) << 3) << 2) + lane] = v[m];
+    }
+}
+
 // One lane-varying layer r of a contiguous tile (c = 0) swept in shared memory.
 template <bool INV>
 __device__ __forceinline__ void smem_layer(uint4 *s, int g, int r, const uint8_t *mt, uint32_t cv,
@@ -160,6 +213,8 @@ __device__ __forceinline__ void prefetch_tables(const FftPassArgs &a, const uint
 __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int g = a.g, c = a.c, uf = a.uf, gt = g - uf;
+    // rows [uf, ul) run limb-wise (only the contiguous bottom pass: rows 3, 4)
+    const int ul = (c == 0 && uf == 3 && g >= 5) ? 5 : uf;
     const uint32_t tile = 1u << (g + c);
     const int NB = a.nbuf;
     uint4 *const buf0 = reinterpret_cast<uint4 *>(smem);  // buffer b at buf0 + b * tile
@@ -285,9 +340,16 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         if (tn < ntiles) prefetch_tables(a, cnext, stab);
 
         if (a.mode != 1) {  // forward layers g_f-1 .. 0
-            for (int r_hi = a.g_f - 1; r_hi >= uf; r_hi -= 3) {
-                const int r_lo = max(uf, r_hi - 2);
+            for (int r_hi = a.g_f - 1; r_hi >= ul; r_hi -= 3) {
+                const int r_lo = max(ul, r_hi - 2);
                 run_subpass<false>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab, a.d_shfl);
+                __syncthreads();
+            }
+            if (ul > uf && a.g_f > uf) {  // rows 3, 4 limb-wise
+                if (a.g_f >= 5)
+                    limb_subpass<2, false>(s, g, uf, ctab, a.d_shfl);
+                else
+                    limb_subpass<1, false>(s, g, uf, ctab, a.d_shfl);
                 __syncthreads();
             }
             for (int r = min(uf, a.g_f) - 1; r >= 0; r--) {
@@ -307,7 +369,11 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
                 smem_layer<true>(s, g, r, mt, cval[r], a.d_val);
                 __syncthreads();
             }
-            for (int r_lo = uf; r_lo < g; r_lo += 3) {
+            if (ul > uf) {  // rows 3, 4 limb-wise
+                limb_subpass<2, true>(s, g, uf, ctab, a.d_shfl);
+                __syncthreads();
+            }
+            for (int r_lo = ul; r_lo < g; r_lo += 3) {
                 const int r_hi = min(g - 1, r_lo + 2);
                 run_subpass<true>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab, a.d_shfl);
                 __syncthreads();
@@ -449,8 +515,10 @@ size_t pass_smem(int g, int c, int uf, bool needs_mt, bool from_g, int nbuf) {
 int make_pass(int k_lo, int g, int c, int uf, int mode, int g_f, PassTableFn src, FftPassCfg *p,
               int nbuf = 2) {
     // register sub-passes need a warp's 32 lanes inside the column bits and
-    // the rows below the sub-pass, so that the lanes share the multiplier
-    if (uf < g && c + uf < 5) return -1;
+    // the rows below the sub-pass, so that the lanes share the multiplier; a
+    // contiguous pass may start them at row 3 (rows 3, 4 limb-wise)
+    const bool limb34 = c == 0 && uf == 3 && g >= 5;
+    if (uf < g && c + uf < 5 && !limb34) return -1;
     int rc = (src ? src : cached_pass_tables)(k_lo, g, uf, &p->d_val, &p->d_shfl);
     if (rc) return rc;
     p->k_lo = k_lo;
@@ -460,8 +528,10 @@ int make_pass(int k_lo, int g, int c, int uf, int mode, int g_f, PassTableFn src
     p->mode = mode;
     p->g_f = g_f;
     p->needs_mt = (uf > 0) || mode == 2;
-    // one buffer only where two CTAs then fit an SM (no product table)
+    // one buffer where two CTAs then fit an SM (no product table), or where
+    // two buffers would not fit
     p->nbuf = (nbuf == 1 && !p->needs_mt) ? 1 : 2;
+    if (pass_smem(g, c, uf, p->needs_mt, false, p->nbuf) > kMaxPassSmem) p->nbuf = 1;
     p->smem = pass_smem(g, c, uf, p->needs_mt, false, p->nbuf);
     p->threads = std::max(32, std::min(p->nbuf == 1 ? 256 : 512, (1 << (g + c)) / 2));
     return 0;
@@ -509,7 +579,7 @@ int plan_fft_forward(int M, int log_p, PassList &out, PassTableFn src, int depth
     if (rc) return rc;
     const int gl = std::min(log_p, kFftTileLog);
     FftPassCfg p;
-    if ((rc = make_pass(0, gl, 0, std::min(5, gl), 0, gl, src, &p))) return rc;
+    if ((rc = make_pass(0, gl, 0, bottom_uf(gl), 0, gl, src, &p))) return rc;
     (void)M;
     return push_pass(out, p);
 }
@@ -518,7 +588,7 @@ int plan_fft_inverse(int M, PassList &out, PassTableFn src, int depth, int nbuf)
     out.n = 0;
     const int gl = std::min(M, kFftTileLog);
     FftPassCfg p;
-    int rc = make_pass(0, gl, 0, std::min(5, gl), 1, gl, src, &p);
+    int rc = make_pass(0, gl, 0, bottom_uf(gl), 1, gl, src, &p);
     if (rc || (rc = push_pass(out, p))) return rc;
     return global_passes(kFftTileLog, M, true, src, out, depth, nbuf);
 }
@@ -531,7 +601,7 @@ int plan_fft_fused(int M, int log_p, PassList &fwd_global, FftPassCfg &local, Pa
     if (rc) return rc;
     const int gl = std::min(M, kFftTileLog);
     const int gf = std::min(log_p, kFftTileLog);
-    if ((rc = make_pass(0, gl, 0, std::min(5, gl), 2, gf, src, &local))) return rc;
+    if ((rc = make_pass(0, gl, 0, bottom_uf(gl), 2, gf, src, &local))) return rc;
     return global_passes(kFftTileLog, M, true, src, inv_global, depth, nbuf);
 }
 

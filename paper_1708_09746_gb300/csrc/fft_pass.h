@@ -79,6 +79,12 @@ int plan_fft_fused(int M, int log_p, PassList &fwd_global, FftPassCfg &local, Pa
 
 // Layers of the contiguous bottom pass and of each strided pass.
 constexpr int kFftTileLog = 12;
+// Dynamic shared memory one CTA may use (227 KiB).
+constexpr size_t kMaxPassSmem = 232448;
+// First row of a contiguous bottom pass of g layers with warp-uniform
+// multipliers: rows 0..2 use the F~_{2^8} product table, rows 3, 4 the
+// limb-wise shuffle sub-pass, the rest whole-element shuffle sub-passes.
+inline int bottom_uf(int g) { return g >= 5 ? 3 : g; }
 constexpr int kFftGlobalMax = 7;  // keeps c = 12 - g >= 5 (warp-uniform multipliers)
 
 int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,

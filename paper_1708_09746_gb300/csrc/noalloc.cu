@@ -43,11 +43,11 @@ static_assert(2 * (16ull << kMaxLog) + 2 * (8ull << (kMaxLog - 1)) + 1024 <= kSc
               "scratch holds the largest allowed product");
 
 // Pass table sets that products with N <= 2^18 use: contiguous bottom passes
-// (k_lo = 0, g = 0 .. 12, uf = min(5, g)) and one strided pass above them
+// (k_lo = 0, g = 0 .. 12, uf = bottom_uf(g)) and one strided pass above them
 // (k_lo = 12, g = 1 .. 6, uf = 0).
 constexpr int kLocalSets = kFftTileLog + 1;
 constexpr int kGlobalSets = kMaxLog - kFftTileLog;
-constexpr size_t kPassWords = 96 * 1024;
+constexpr size_t kPassWords = 288 * 1024;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 static __device__ __align__(256) DevTables g_tables;
@@ -89,7 +89,7 @@ int static_pass_tables(int k_lo, int g, int uf, const uint32_t **d_val, const ui
     DevState *st = state_of_current(nullptr);
     if (!st || !st->ready) return -3;
     const SetOffsets *o = nullptr;
-    if (k_lo == 0 && g >= 0 && g < kLocalSets && uf == (g < 5 ? g : 5)) o = &st->local[g];
+    if (k_lo == 0 && g >= 0 && g < kLocalSets && uf == bottom_uf(g)) o = &st->local[g];
     if (k_lo == kFftTileLog && g >= 1 && g <= kGlobalSets && uf == 0) o = &st->global[g];
     if (!o) return -1;
     *d_val = st->pass_words + o->val;
@@ -127,7 +127,7 @@ int setup_current_device() {
             return true;
         };
         for (int g = 0; g < kLocalSets; g++)
-            if (!add(0, g, g < 5 ? g : 5, &st->local[g])) return GF2X_ENOMEM;
+            if (!add(0, g, bottom_uf(g), &st->local[g])) return GF2X_ENOMEM;
         for (int g = 1; g <= kGlobalSets; g++)
             if (!add(kFftTileLog, g, 0, &st->global[g])) return GF2X_ENOMEM;
         if (cudaMemcpy(st->tables, &g_host_tables, sizeof(DevTables), cudaMemcpyHostToDevice) !=

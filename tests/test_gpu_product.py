@@ -29,7 +29,9 @@ def test_c0_2pow20_seed0():
 SMALL = [(1, 1), (1, 64), (64, 1), (64, 64), (65, 63), (127, 129), (128, 128),
          (200, 3000), (3000, 200), (4096, 4096), (4097, 1), (1, 4097), (640, 700),
          (64 * 33, 64 * 31 + 5), (8191, 8193), (65536, 65536), (65536, 65535),
-         (100000, 3), (131072 + 64, 131072 - 64)]
+         (100000, 3), (131072 + 64, 131072 - 64),
+         # b of 9 .. 16 words: its forward transform stops at layer 3
+         (64 * 100, 64 * 16), (64 * 100, 64 * 9), (64 * 300, 64 * 32)]
 
 
 @pytest.mark.parametrize("na,nb", SMALL)
