@@ -84,7 +84,8 @@ def _max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -224,8 +225,8 @@ def run_reference(args):
         "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": v / PAPER_MS_2_28, "dtype": "u64",
         "data": "synthetic",
-        "config": {"workload": "single %d x %d-bit product (%s)" % (na, nb, args.workload),
-                   "na_bits": na, "nb_bits": nb},
+        "config": {"workload": "single %d x %d-bit product (%s), uniform random bits"
+                   % (na, nb, args.workload), "na_bits": na, "nb_bits": nb},
         "cpu_baseline": {"kind": "oracle", "cores": vals[0]["cores"],
                          "sample": vals[0]["sample"], "value": v, "unit": "ms"},
         "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
