@@ -203,13 +203,13 @@ __device__ __forceinline__ void prefetch_tables(const FftPassArgs &a, const uint
 }
 
 // Persistent kernel: each CTA walks the tiles blockIdx.x, +gridDim.x, ...
-// with two tile buffers.  While one tile is computed, the next one is being
-// loaded by bulk copies (TMA) and the previous one stored; warp 0 issues all
-// copies.  The first pass of a transform reads the 64-bit blocks instead and
-// applies changeRepr on the way in; when the pass has room (no product table)
-// those blocks are also staged ahead by bulk copies, otherwise they are read
-// with ordinary loads.  The shuffle tables of the next tile's multipliers
-// are copied in asynchronously while the current tile is computed.
+// with one or two tile buffers.  While one tile is computed, the next one is
+// being loaded by bulk copies (TMA) and the previous one stored; warp 0 issues
+// all copies.  The first strided pass of a transform loads the changeRepr'd
+// blocks (P elements, read periodically); a bottom pass that is also the
+// first reads the 64-bit blocks and applies changeRepr on the way in.  The
+// shuffle tables of the next tile's multipliers are copied in
+// asynchronously while the current tile is computed.
 __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int g = a.g, c = a.c, uf = a.uf, gt = g - uf;
@@ -225,30 +225,25 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     uint64_t *bar = reinterpret_cast<uint64_t *>(cnext + 32);                 // [4]
     unsigned char *tail = reinterpret_cast<unsigned char *>(bar + 4);
     const bool from_g = a.g64 != nullptr;
-    const bool pipe = !from_g;                // tiles of F by bulk copies
-    // 64-bit blocks staged by bulk copies: needs room (no product table) and
-    // rows of at least 16 bytes (c >= 1; strided passes have c >= 5)
-    const bool gpipe = from_g && !a.needs_mt && c >= 1;
-    uint64_t *g64s = reinterpret_cast<uint64_t *>(tail);             // [tile] if gpipe
-    // if gpipe: the changeRepr tables (8 x 256 elements, 32 KiB) after the blocks
-    uint4 *chr_s = reinterpret_cast<uint4 *>(tail + 8 * (size_t)tile);
-    uint8_t *mt = tail + (gpipe ? 8 * (size_t)tile + 32768 : 0);     // 64 KiB if needed
+    const bool pipe = !from_g;                // tiles by bulk copies
+    uint8_t *mt = tail;                       // 64 KiB if needed
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const TileGeom G{c, a.k_lo, g, 4};
-    const TileGeom G8{c, a.k_lo, g, 3};
     // tiles of every product: t = (product << tiles_log) | tile
     const int tiles_log = a.M - g - c;
     const uint64_t ntiles = (uint64_t)a.count << tiles_log;
     const uint64_t tmask = (1ull << tiles_log) - 1;
     const uint32_t cmask = (1u << c) - 1;
-    // The 64-bit blocks of tile t: rows of the same shape at the index taken
-    // modulo P.  The pass's layers lie below log2 P, so only the tile's high
-    // bits are reduced: the block tile number keeps the middle bits and the
-    // high bits modulo P >> (k_lo + g).
+    // Source of tile t.  Normally the tile itself; the first pass of a
+    // transform reads the changeRepr'd blocks (a.Fsrc, P elements) at the
+    // index taken modulo P: the pass's layers lie below log2 P, so only the
+    // tile's high bits are reduced (the fan-out of the layers above).
     const int mid_bits = a.k_lo - c;
-    auto g_tile_src = [&](uint64_t t) { return a.g64 + (t >> tiles_log) * a.strideW; };
-    auto g_tile_of = [&](uint64_t tt) {
+    const uint4 *src_base = a.Fsrc ? a.Fsrc : a.F;
+    auto src_of = [&](uint64_t t) { return src_base + (t >> tiles_log) * a.strideF; };
+    auto src_tile = [&](uint64_t tt) -> uint64_t {
+        if (!a.Fsrc) return tt;
         return (((tt >> mid_bits) & (a.pmask >> (a.k_lo + g))) << mid_bits) |
                (tt & ((1ull << mid_bits) - 1));
     };
@@ -262,21 +257,13 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         uint4 *dst = reinterpret_cast<uint4 *>(mt);
         for (int i = threadIdx.x; i < 4096; i += blockDim.x) dst[i] = __ldg(src + i);
     }
-    if (gpipe) {
-        const uint4 *src = &a.T->chr_in[0][0];
-        for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) chr_s[i] = __ldg(src + i);
-    }
     if ((int)threadIdx.x < g && blockIdx.x < ntiles)
         cnext[threadIdx.x] = tile_cval(a, blockIdx.x & tmask, threadIdx.x);
     __syncthreads();
     if (blockIdx.x < ntiles) {
         prefetch_tables(a, cnext, stab);
         if (warp == 0 && pipe)
-            tile_load_issue(G, a.F + (blockIdx.x >> tiles_log) * a.strideF, blockIdx.x & tmask,
-                            buf0, &bar[0], lane);
-        if (warp == 0 && gpipe)
-            tile_load_issue(G8, g_tile_src(blockIdx.x), g_tile_of(blockIdx.x & tmask), g64s, &bar[2],
-                            lane);
+            tile_load_issue(G, src_of(blockIdx.x), src_tile(blockIdx.x & tmask), buf0, &bar[0], lane);
     }
 
     bool aborted = false, prefetched = false;
@@ -293,14 +280,13 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
             if (NB == 2 && warp == 0 && tn < ntiles) {
                 bulk_wait_read_all();  // the stores out of buf[b^1] have read it
                 __syncwarp();
-                tile_load_issue(G, a.F + (tn >> tiles_log) * a.strideF, tn & tmask,
-                                buf0 + (b ? 0 : tile), &bar[b ^ 1], lane);
+                tile_load_issue(G, src_of(tn), src_tile(tn & tmask), buf0 + (b ? 0 : tile),
+                                &bar[b ^ 1], lane);
                 prefetched = true;
             }
             ok = mbar_wait_bounded(&bar[b], NB == 2 ? (i >> 1) & 1 : i & 1);
         } else {
             if (warp == 0) bulk_wait_read_all();  // the stores out of buf[b] have read it
-            if (gpipe) ok = mbar_wait_bounded(&bar[2], i & 1);
         }
         cp_async_wait_all();
         if (!__syncthreads_and(ok)) {
@@ -314,15 +300,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         }
         if (threadIdx.x < 32) cval[threadIdx.x] = cnext[threadIdx.x];
         const uint64_t base = tile_base(G, tt);
-        if (gpipe) {
-            for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) {
-                const uint64_t w = g64s[q];
-                uint4 acc = make_uint4(0, 0, 0, 0);
-#pragma unroll
-                for (int p = 0; p < 8; p++) acc = xor4(acc, chr_s[p * 256 + ((w >> (8 * p)) & 255)]);
-                s[q] = acc;
-            }
-        } else if (from_g) {
+        if (from_g) {
             const uint64_t *gy = a.g64 + y * a.strideW;
             for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) {
                 const uint64_t idx = base | ((uint64_t)(q >> c) << a.k_lo) | (q & cmask);
@@ -330,11 +308,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
             }
         }
         __syncthreads();
-        // prefetch the next tile's blocks and multipliers' tables
-        if (gpipe && warp == 0 && tn < ntiles) {
-            tile_load_issue(G8, g_tile_src(tn), g_tile_of(tn & tmask), g64s, &bar[2], lane);
-            prefetched = true;
-        }
+        // the next tile's multipliers and their tables
         if ((int)threadIdx.x < g && tn < ntiles) cnext[threadIdx.x] = tile_cval(a, tn & tmask, threadIdx.x);
         __syncthreads();
         if (tn < ntiles) prefetch_tables(a, cnext, stab);
@@ -386,19 +360,13 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         if (pipe && NB == 1 && warp == 0 && tn < ntiles) {
             bulk_wait_read_all();
             __syncwarp();
-            tile_load_issue(G, a.F + (tn >> tiles_log) * a.strideF, tn & tmask, buf0, &bar[0],
-                            lane);
+            tile_load_issue(G, src_of(tn), src_tile(tn & tmask), buf0, &bar[0], lane);
         }
     }
     if (aborted) {
         if (threadIdx.x == 0) atomicExch(a.status, -4);  // GF2X_ETIMEOUT
         // let a prefetch already in flight land before the CTA exits
-        if (prefetched && threadIdx.x == 0) {
-            if (pipe)
-                mbar_wait_bounded(&bar[(i & 1) ^ 1], ((i + 1) >> 1) & 1);
-            else
-                mbar_wait_bounded(&bar[2], (i + 1) & 1);
-        }
+        if (prefetched && threadIdx.x == 0) mbar_wait_bounded(&bar[(i & 1) ^ 1], ((i + 1) >> 1) & 1);
     }
     cp_async_wait_all();
     if (warp == 0) bulk_wait_all();
@@ -500,14 +468,12 @@ int cached_pass_tables(int k_lo, int g, int uf, const uint32_t **d_val, const ui
     return 0;
 }
 
-// Shared memory of a pass: one or two tile buffers, the shuffle tables of the tile's
-// multipliers and their staged byte slices, the multipliers, four mbarriers,
-// then the staged 64-bit blocks and the changeRepr tables (first pass without
-// product table) and the F~_{2^8} product table if needed.
-size_t pass_smem(int g, int c, int uf, bool needs_mt, bool from_g, int nbuf) {
+// Shared memory of a pass: one or two tile buffers, the shuffle tables of the
+// tile's multipliers and their staged byte slices, the multipliers, four
+// mbarriers, then the F~_{2^8} product table if needed.
+size_t pass_smem(int g, int c, int uf, bool needs_mt, int nbuf) {
     size_t b = ((size_t)16 * nbuf) << (g + c);
     b += (size_t)(g - uf) * 224 * 4 * 5 + 64 * 4 + 4 * 8;
-    if (from_g && !needs_mt && c >= 1) b += ((size_t)8 << (g + c)) + 32768;
     if (needs_mt) b += 65536;
     return b;
 }
@@ -531,8 +497,8 @@ int make_pass(int k_lo, int g, int c, int uf, int mode, int g_f, PassTableFn src
     // one buffer where two CTAs then fit an SM (no product table), or where
     // two buffers would not fit
     p->nbuf = (nbuf == 1 && !p->needs_mt) ? 1 : 2;
-    if (pass_smem(g, c, uf, p->needs_mt, false, p->nbuf) > kMaxPassSmem) p->nbuf = 1;
-    p->smem = pass_smem(g, c, uf, p->needs_mt, false, p->nbuf);
+    if (pass_smem(g, c, uf, p->needs_mt, p->nbuf) > kMaxPassSmem) p->nbuf = 1;
+    p->smem = pass_smem(g, c, uf, p->needs_mt, p->nbuf);
     p->threads = std::max(32, std::min(p->nbuf == 1 ? 256 : 512, (1 << (g + c)) / 2));
     return 0;
 }
@@ -623,10 +589,11 @@ static int resident_ctas(int threads, size_t smem) {
 
 int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,
                     const uint4 *FA, const DevTables *T, int *status, cudaStream_t s, int count,
-                    uint64_t strideF, uint64_t strideW) {
+                    uint64_t strideF, uint64_t strideW, const uint4 *Fsrc) {
     ensure_smem_attr(reinterpret_cast<const void *>(k_fft_pass), 227 * 1024);
     FftPassArgs a;
     a.F = F;
+    a.Fsrc = Fsrc;
     a.g64 = g64;
     a.pmask = P ? P - 1 : 0;
     a.FA = FA;
@@ -647,7 +614,7 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
     a.strideW = strideW;
     a.nbuf = p.nbuf;
     const uint64_t tiles = ((1ull << M) >> (p.g + p.c)) * (uint64_t)count;
-    const size_t smem = pass_smem(p.g, p.c, p.uf, p.needs_mt, g64 != nullptr, p.nbuf);
+    const size_t smem = pass_smem(p.g, p.c, p.uf, p.needs_mt, p.nbuf);
     // persistent CTAs: as many as are resident at once; a CTA alone on its SM
     // (shared memory too large for two) gets the full 512 threads
     int threads = p.threads;

@@ -27,6 +27,7 @@ struct FftPassCfg {
 
 struct FftPassArgs {
     uint4 *F;
+    const uint4 *Fsrc;    // non-null: tiles load from Fsrc[idx & pmask] (the fan-out)
     const uint64_t *g64;  // non-null: read changeRepr(g64[idx & pmask]) instead of F
     uint64_t pmask;
     const uint4 *FA;      // mode 2: the other operand's transform
@@ -89,7 +90,8 @@ constexpr int kFftGlobalMax = 7;  // keeps c = 12 - g >= 5 (warp-uniform multipl
 
 int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,
                     const uint4 *FA, const DevTables *T, int *status, cudaStream_t s,
-                    int count = 1, uint64_t strideF = 0, uint64_t strideW = 0);
+                    int count = 1, uint64_t strideF = 0, uint64_t strideW = 0,
+                    const uint4 *Fsrc = nullptr);
 
 void launch_pointmul_mt(const uint4 *A, const uint4 *B, uint4 *C, uint64_t n, const DevTables *T,
                         cudaStream_t s);

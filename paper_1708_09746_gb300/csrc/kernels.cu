@@ -485,6 +485,30 @@ __global__ void k_chrepr(const uint64_t *__restrict__ g, uint64_t pmask, uint4 *
     }
 }
 
+// changeRepr of `count` operands ahead of their first strided FFT pass:
+// F[i] = phi(g[i]) for i < P (product y at g + y * strideW, F + y * strideF),
+// phi by the 8-bit tables held in shared memory (32 KiB per CTA).
+__global__ void __launch_bounds__(256) k_chrepr_stage(const uint64_t *__restrict__ g, uint64_t P,
+                                                      uint64_t strideW, uint4 *__restrict__ F,
+                                                      uint64_t strideF,
+                                                      const DevTables *__restrict__ T) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint4 *tab = reinterpret_cast<uint4 *>(smem_raw);
+    const uint4 *src = &T->chr_in[0][0];
+    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) tab[i] = __ldg(src + i);
+    __syncthreads();
+    g += blockIdx.y * strideW;
+    F += blockIdx.y * strideF;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < P;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t w = g[i];
+        uint4 acc = make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int p = 0; p < 8; p++) acc = xor4(acc, tab[p * 256 + ((w >> (8 * p)) & 255)]);
+        F[i] = acc;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // changeRepr^-1 and InterleavedCombine (Sec. 2.1): psi(F[j]) is a polynomial
 // of degree < 128 in z; z -> x and y -> x^64 add its high word into the next
@@ -858,6 +882,13 @@ template uint64_t run_basis_cvt<uint64_t>(uint64_t *, int, const LevelList &, in
                                           int, uint64_t, const BcvtTune &);
 template uint64_t run_basis_cvt<uint4>(uint4 *, int, const LevelList &, int, cudaStream_t, int,
                                        uint64_t, const BcvtTune &);
+
+void launch_chrepr_stage(const uint64_t *g, uint64_t P, uint64_t strideW, uint4 *F,
+                         uint64_t strideF, int count, const DevTables *T, cudaStream_t s) {
+    const uint64_t per = std::max<uint64_t>(1, (uint64_t)num_sms() * 4 / (uint64_t)std::max(count, 1));
+    dim3 grid((unsigned)std::max<uint64_t>(1, std::min<uint64_t>((P + 255) / 256, per)), count);
+    k_chrepr_stage<<<grid, 256, 32768, s>>>(g, P, strideW, F, strideF, T);
+}
 
 void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const DevTables *T,
                    cudaStream_t s) {

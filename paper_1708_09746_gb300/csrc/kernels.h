@@ -72,6 +72,11 @@ template <typename T>
 uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStream_t s,
                        int count = 1, uint64_t stride = 0, const BcvtTune &tune = BcvtTune());
 
+// changeRepr of the P blocks of `count` operands (product y at g + y * strideW)
+// into F + y * strideF, ahead of their first strided FFT pass.
+void launch_chrepr_stage(const uint64_t *g, uint64_t P, uint64_t strideW, uint4 *F,
+                         uint64_t strideF, int count, const DevTables *T, cudaStream_t s);
+
 void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const DevTables *T,
                    cudaStream_t s);
 

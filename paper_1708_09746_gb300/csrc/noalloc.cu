@@ -38,8 +38,11 @@ constexpr size_t kScratchBytes = (size_t)GF2X_NOALLOC_SCRATCH_BYTES;
 constexpr int kMaxLog = 18;  // log2 of GF2X_NOALLOC_MAX_FFT_POINTS
 static_assert((1ull << kMaxLog) == GF2X_NOALLOC_MAX_FFT_POINTS, "limit");
 // The workspace of the largest allowed product: two 16-byte arrays of 2^18
-// points and two padded operands of at most 2^17 words.
-static_assert(2 * (16ull << kMaxLog) + 2 * (8ull << (kMaxLog - 1)) + 1024 <= kScratchBytes,
+// points, two padded operands of at most 2^17 words and the changeRepr'd
+// blocks of one operand (2^17 elements).
+static_assert(2 * (16ull << kMaxLog) + 2 * (8ull << (kMaxLog - 1)) + (16ull << (kMaxLog - 1)) +
+                      1280 <=
+                  kScratchBytes,
               "scratch holds the largest allowed product");
 
 // Pass table sets that products with N <= 2^18 use: contiguous bottom passes

@@ -67,7 +67,10 @@ int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits, PassTableFn src,
     p->off_fb = up(p->off_fa + 16 * p->N);
     p->off_wa = up(p->off_fb + 16 * p->N);
     p->off_wb = up(p->off_wa + 8 * p->Pa);
-    p->ws_bytes = up(p->off_wb + 8 * p->Pb);
+    p->off_st = up(p->off_wb + 8 * p->Pb);
+    // fft_a ends with its bottom pass; fft_b holds strided passes only
+    const bool staged = p->fft_a.n > 1 || p->fft_b.n > 0;
+    p->ws_bytes = up(p->off_st + (staged ? 16 * std::max(p->Pa, p->Pb) : 0));
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         cudaGetLastError();
         return -3;
@@ -85,6 +88,7 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
     uint4 *FB = reinterpret_cast<uint4 *>(base + p->off_fb);
     uint64_t *WA = reinterpret_cast<uint64_t *>(base + p->off_wa);
     uint64_t *WB = reinterpret_cast<uint64_t *>(base + p->off_wb);
+    uint4 *ST = reinterpret_cast<uint4 *>(base + p->off_st);
     const uint64_t sF = ws_stride / 16, sW = ws_stride / 8;
     auto begin = [&](int stage) {
         if (hook) hook->begin(stage);
@@ -101,10 +105,14 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
     begin(ST_BCVT);
     end(run_basis_cvt<uint64_t>(WA, p->pa_log, p->lv_a, 0, s, count, sW, p->tune.bcvt));
     begin(ST_FFT_A);
+    // with strided passes: changeRepr into ST, which the first pass reads
+    // periodically; a lone bottom pass reads the blocks and converts them itself
+    const bool st_a = p->fft_a.n > 1;
+    if (st_a) launch_chrepr_stage(WA, p->Pa, sW, ST, sF, count, T, s);
     for (int i = 0; i < p->fft_a.n; i++)
-        launch_fft_pass(p->fft_a.v[i], p->M, FA, i == 0 ? WA : nullptr, p->Pa, nullptr, T, st, s,
-                        count, sF, sW);
-    end(p->fft_a.n);
+        launch_fft_pass(p->fft_a.v[i], p->M, FA, (i == 0 && !st_a) ? WA : nullptr, p->Pa, nullptr, T,
+                        st, s, count, sF, sW, (i == 0 && st_a) ? ST : nullptr);
+    end(p->fft_a.n + (st_a ? 1 : 0));
     // the same for b, then its top FFT layers
     if (b_ready) cudaStreamWaitEvent(s, b_ready, 0);
     begin(ST_SPLIT);
@@ -113,10 +121,11 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
     begin(ST_BCVT);
     end(run_basis_cvt<uint64_t>(WB, p->pb_log, p->lv_b, 0, s, count, sW, p->tune.bcvt));
     begin(ST_FFT_B);
+    if (p->fft_b.n > 0) launch_chrepr_stage(WB, p->Pb, sW, ST, sF, count, T, s);
     for (int i = 0; i < p->fft_b.n; i++)
-        launch_fft_pass(p->fft_b.v[i], p->M, FB, i == 0 ? WB : nullptr, p->Pb, nullptr, T, st, s,
-                        count, sF, sW);
-    end(p->fft_b.n);
+        launch_fft_pass(p->fft_b.v[i], p->M, FB, nullptr, p->Pb, nullptr, T, st, s, count, sF, sW,
+                        i == 0 ? ST : nullptr);
+    end(p->fft_b.n + (p->fft_b.n > 0));
     // bottom layers of FFT(b), pointmul, bottom layers of iFFT_LCH
     begin(ST_FUSED);
     launch_fft_pass(p->fused, p->M, FB, p->fft_b.n == 0 ? WB : nullptr, p->Pb, FA, T, st, s, count,

@@ -34,8 +34,10 @@ struct gf2x_plan {
     // does pointmul and the bottom inverse layers; the inverse top layers.
     gf2x::PassList fft_a, fft_b, ifft_top;
     gf2x::FftPassCfg fused;
-    // workspace layout (bytes): FA | FB | WA | WB
-    size_t off_fa, off_fb, off_wa, off_wb, ws_bytes;
+    // workspace layout (bytes): FA | FB | WA | WB | ST (the changeRepr'd blocks
+    // of the operand whose first strided pass comes next, max(Pa, Pb) elements,
+    // present when a transform has strided passes)
+    size_t off_fa, off_fb, off_wa, off_wb, off_st, ws_bytes;
     int device;
     std::mutex mu;
     void *owned_ws = nullptr;
