@@ -246,18 +246,28 @@ def fft_work(na, nb):
     return 4 * (N // 2) * (lg(na_w) + lg(nb_w) + M), N, M, lg(na_w), lg(nb_w)
 
 
-def fft_hbm_bytes(N, M, la, lb):
-    """Bytes the FFT pass kernels of one product move (tile in + tile out per
-    pass, the changeRepr passes reading 8-byte blocks, the fused pass also
-    reading the other transform)."""
-    def passes(layers):
-        return 1 + max(0, -(-(layers - 12) // 8))
+def fft_hbm_bytes(N, M, la, lb, depth=7):
+    """Bytes the FFT stages of one product move at least: changeRepr reading
+    the P 8-byte blocks and writing P elements (when a strided pass follows),
+    each pass a tile in and a tile out (the first strided pass reading only
+    the P staged elements, a lone bottom pass the P blocks), the fused pass
+    also reading the other transform.  Passes: layers 12 .. log2 P (forward)
+    or M (inverse) in strided passes of at most `depth` layers, then the
+    4096-element bottom pass."""
+    def strided(layers):
+        return max(0, -(-(layers - 12) // depth))
     b = 0
     for L in (la, lb):
-        npass = passes(L)
-        b += (npass - 1) * 32 * N + (8 * N + 16 * N)  # first pass reads blocks
+        P = 1 << L
+        s = strided(L)
+        if s:
+            b += 24 * P                              # changeRepr: blocks in, elements out
+            b += 16 * P + 16 * N                     # first strided pass
+            b += (s - 1) * 32 * N + 32 * N           # other strided passes, bottom pass
+        else:
+            b += 8 * P + 16 * N                      # bottom pass converts the blocks
     b += 16 * N                                      # fused pass reads FA
-    b += (passes(M) - 1) * 32 * N                    # inverse top passes
+    b += strided(M) * 32 * N                         # inverse top passes
     return b
 
 
@@ -503,7 +513,8 @@ def run_ours(args):
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     peak_lmul = 152 * 32 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / SHFL_PER_LIMB_MUL
     ach_lmul = work / (fft_ms / 1e3)
-    roof = {"bound": "alu", "kernel": "k_fft_pass (all FFT_LCH / iFFT_LCH passes)",
+    roof = {"bound": "alu", "kernel": "k_fft_pass (all FFT_LCH / iFFT_LCH passes; the "
+                                      "stage times include the changeRepr kernel ahead of them)",
             "achieved": ach_lmul / 1e9, "peak": peak_lmul / 1e9,
             "unit": "G limb-mult/s", "frac": ach_lmul / peak_lmul, "traffic": None,
             "work_per_launch": work / max(1, fft_launches),
@@ -511,7 +522,8 @@ def run_ours(args):
             "share_of_step": fft_ms / max(1e-9, total_stage_ms),
             "peak_source": "derived: 152 SMs x 32 lanes x max SM clock / 7 warp shuffles "
                            "per F~_{2^32} limb product"}
-    fbytes = fft_hbm_bytes(N, M, la, lb)
+    plan_depth = max(1, min(7, int(tuned.get("fft_depth", 7))))
+    fbytes = fft_hbm_bytes(N, M, la, lb, plan_depth)
     roof_hbm = {"bound": "hbm", "kernel": "k_fft_pass", "achieved": fbytes / (fft_ms / 1e3) / 1e9,
                 "peak": hbm, "unit": "GB/s", "frac": fbytes / (fft_ms / 1e3) / 1e9 / hbm,
                 "bytes_per_product": fbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
