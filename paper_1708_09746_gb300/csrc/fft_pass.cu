@@ -152,7 +152,7 @@ __device__ __forceinline__ void limb_subpass(uint4 *s, int g, int uf, const uint
 
 // One lane-varying layer r of a contiguous tile (c = 0) swept in shared memory.
 template <bool INV>
-__device__ __forceinline__ void smem_layer(uint4 *s, int g, int r, const uint8_t *mt, uint32_t cv,
+__device__ __forceinline__ void smem_layer(uint4 *s, int g, int r, const MtRef &mt, uint32_t cv,
                                            const uint32_t *__restrict__ d_val) {
     const uint32_t half = 1u << (g - 1);
     const uint32_t voff = (1u << g) - (1u << (g - r));
@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     const bool from_g = a.g64 != nullptr;
     const bool pipe = !from_g;                // tiles by bulk copies
     uint8_t *mt = tail;                       // 64 KiB if needed
+    uint32_t *v7tab = reinterpret_cast<uint32_t *>(tail + 65536);  // kV7TabBytes with mt
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const TileGeom G{c, a.k_lo, g, 4};
@@ -256,7 +257,9 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         const uint4 *src = reinterpret_cast<const uint4 *>(a.T->mul8);
         uint4 *dst = reinterpret_cast<uint4 *>(mt);
         for (int i = threadIdx.x; i < 4096; i += blockDim.x) dst[i] = __ldg(src + i);
+        v7tab_fill(v7tab, a.T->mul8);
     }
+    const MtRef M = mt_ref(mt, v7tab);
     if ((int)threadIdx.x < g && blockIdx.x < ntiles)
         cnext[threadIdx.x] = tile_cval(a, blockIdx.x & tmask, threadIdx.x);
     __syncthreads();
@@ -327,20 +330,20 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
                 __syncthreads();
             }
             for (int r = min(uf, a.g_f) - 1; r >= 0; r--) {
-                smem_layer<false>(s, g, r, mt, cval[r], a.d_val);
+                smem_layer<false>(s, g, r, M, cval[r], a.d_val);
                 __syncthreads();
             }
         }
         if (a.mode == 2) {  // pointmul with the other operand's transform
             for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) {
                 const uint64_t idx = base | ((uint64_t)(q >> c) << a.k_lo) | (q & cmask);
-                s[q] = mt_gmul128(mt, s[q], __ldg(a.FA + y * a.strideF + idx));
+                s[q] = mt_gmul128(M, s[q], __ldg(a.FA + y * a.strideF + idx));
             }
             __syncthreads();
         }
         if (a.mode != 0) {  // inverse layers 0 .. g-1
             for (int r = 0; r < min(uf, g); r++) {
-                smem_layer<true>(s, g, r, mt, cval[r], a.d_val);
+                smem_layer<true>(s, g, r, M, cval[r], a.d_val);
                 __syncthreads();
             }
             if (ul > uf) {  // rows 3, 4 limb-wise
@@ -380,11 +383,14 @@ __global__ void __launch_bounds__(256) k_pointmul_mt(const uint4 *__restrict__ A
     extern __shared__ __align__(128) unsigned char smem[];
     uint8_t *mt = smem;
     const uint4 *src = reinterpret_cast<const uint4 *>(T->mul8);
+    uint32_t *v7tab = reinterpret_cast<uint32_t *>(smem + 65536);
     for (int i = threadIdx.x; i < 4096; i += blockDim.x) reinterpret_cast<uint4 *>(mt)[i] = __ldg(src + i);
+    v7tab_fill(v7tab, T->mul8);
     __syncthreads();
+    const MtRef M = mt_ref(mt, v7tab);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
-        C[i] = mt_gmul128(mt, A[i], B[i]);
+        C[i] = mt_gmul128(M, A[i], B[i]);
 }
 
 // ===========================================================================
@@ -470,11 +476,12 @@ int cached_pass_tables(int k_lo, int g, int uf, const uint32_t **d_val, const ui
 
 // Shared memory of a pass: one or two tile buffers, the shuffle tables of the
 // tile's multipliers and their staged byte slices, the multipliers, four
-// mbarriers, then the F~_{2^8} product table if needed.
+// mbarriers, then the F~_{2^8} product table and the per-lane v_7 table if
+// needed.
 size_t pass_smem(int g, int c, int uf, bool needs_mt, int nbuf) {
     size_t b = ((size_t)16 * nbuf) << (g + c);
     b += (size_t)(g - uf) * 224 * 4 * 5 + 64 * 4 + 4 * 8;
-    if (needs_mt) b += 65536;
+    if (needs_mt) b += 65536 + kV7TabBytes;
     return b;
 }
 
@@ -627,9 +634,10 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
 
 void launch_pointmul_mt(const uint4 *A, const uint4 *B, uint4 *C, uint64_t n, const DevTables *T,
                         cudaStream_t s) {
-    ensure_smem_attr(reinterpret_cast<const void *>(k_pointmul_mt), 65536);
-    uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 152 * 8);
-    k_pointmul_mt<<<(unsigned)std::max<uint64_t>(1, blocks), 256, 65536, s>>>(A, B, C, n, T);
+    const int smem = 65536 + (int)kV7TabBytes;
+    ensure_smem_attr(reinterpret_cast<const void *>(k_pointmul_mt), smem);
+    uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 152 * 2);
+    k_pointmul_mt<<<(unsigned)std::max<uint64_t>(1, blocks), 256, smem, s>>>(A, B, C, n, T);
 }
 
 }  // namespace gf2x

@@ -42,14 +42,43 @@ __device__ __forceinline__ uint4 shfl_mul128(uint4 v, const ShflTab &T) {
 }
 
 // ---- F~_{2^8} product table: mt[(c << 8) | x] = c * x ----------------------
-__device__ __forceinline__ uint32_t mt_v7(const uint8_t *mt, uint32_t x) {
-    return mt[0x8000u | x];  // x * v_7
+// The products by the constants v_7 and v_7^2 (the reductions X^2 = X + v_{W-1}
+// of every tower level end in them) come from a second table with one copy per
+// lane: word x * 32 + l holds v_7 x (byte 0) and v_7^2 x (byte 1) for lane l,
+// so the 32 lanes of a warp always read 32 different banks.  `v7` points at
+// the calling lane's byte 0 of entry 0 (table base + 4 * lane).
+struct MtRef {
+    const uint8_t *mt;
+    const uint8_t *v7;
+};
+
+constexpr size_t kV7TabBytes = 256 * 32 * 4;
+
+// Fills the per-lane v_7 table (kV7TabBytes) from the global product table.
+__device__ __forceinline__ void v7tab_fill(uint32_t *dst, const uint8_t *__restrict__ mul8) {
+    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) {
+        const uint32_t x = (uint32_t)i >> 5;
+        const uint32_t y = __ldg(mul8 + (0x8000u | x));
+        dst[i] = y | ((uint32_t)__ldg(mul8 + (0x8000u | y)) << 8);
+    }
+}
+
+__device__ __forceinline__ MtRef mt_ref(const uint8_t *mt, const uint32_t *v7tab) {
+    return MtRef{mt, reinterpret_cast<const uint8_t *>(v7tab + (threadIdx.x & 31))};
+}
+
+__device__ __forceinline__ uint32_t mt_v7(const MtRef &M, uint32_t x) {
+    return M.v7[x << 7];  // x * v_7
+}
+
+__device__ __forceinline__ uint32_t mt_v77(const MtRef &M, uint32_t x) {
+    return M.v7[(x << 7) + 1];  // x * v_7^2
 }
 
 // x * v_15 in F~_{2^16}
-__device__ __forceinline__ uint32_t mt_p16(const uint8_t *mt, uint32_t x) {
+__device__ __forceinline__ uint32_t mt_p16(const MtRef &M, uint32_t x) {
     uint32_t x0 = x & 0xff, x1 = x >> 8;
-    return mt_v7(mt, mt_v7(mt, x1)) | (mt_v7(mt, x0 ^ x1) << 8);
+    return mt_v77(M, x1) | (mt_v7(M, x0 ^ x1) << 8);
 }
 
 // A multiplier prepared for the product table: row offsets (leaf << 8) of
@@ -58,15 +87,15 @@ struct MtConst {
     uint32_t r[9];
 };
 
-__device__ __forceinline__ MtConst mt_prep(const uint8_t *mt, uint32_t c) {
+__device__ __forceinline__ MtConst mt_prep(const MtRef &M, uint32_t c) {
     uint32_t h = c >> 16;
-    uint32_t Cs[3] = {c & 0xffff, mt_p16(mt, h), (c & 0xffff) ^ h};
+    uint32_t Cs[3] = {c & 0xffff, mt_p16(M, h), (c & 0xffff) ^ h};
     MtConst m;
 #pragma unroll
     for (int j = 0; j < 3; j++) {
         uint32_t lo = Cs[j] & 0xff, hi = Cs[j] >> 8;
         m.r[3 * j + 0] = lo << 8;
-        m.r[3 * j + 1] = mt_v7(mt, hi) << 8;
+        m.r[3 * j + 1] = mt_v7(M, hi) << 8;
         m.r[3 * j + 2] = (lo ^ hi) << 8;
     }
     return m;
@@ -87,51 +116,51 @@ __device__ __forceinline__ uint32_t mt_cmul32(const uint8_t *mt, uint32_t x, con
     return (a ^ b) | ((d ^ a) << 16);
 }
 
-__device__ __forceinline__ uint4 mt_cmul128(const uint8_t *mt, uint4 v, const MtConst &m) {
-    return make_uint4(mt_cmul32(mt, v.x, m), mt_cmul32(mt, v.y, m), mt_cmul32(mt, v.z, m),
-                      mt_cmul32(mt, v.w, m));
+__device__ __forceinline__ uint4 mt_cmul128(const MtRef &M, uint4 v, const MtConst &m) {
+    return make_uint4(mt_cmul32(M.mt, v.x, m), mt_cmul32(M.mt, v.y, m), mt_cmul32(M.mt, v.z, m),
+                      mt_cmul32(M.mt, v.w, m));
 }
 
 // Generic products (both operands variable) for pointmul.
-__device__ __forceinline__ uint32_t mt_gmul16(const uint8_t *mt, uint32_t a, uint32_t b) {
+__device__ __forceinline__ uint32_t mt_gmul16(const MtRef &M, uint32_t a, uint32_t b) {
     uint32_t a0 = a & 0xff, a1 = a >> 8, b0 = b & 0xff, b1 = b >> 8;
-    uint32_t p0 = mt[(b0 << 8) | a0];
-    uint32_t p1 = mt[(mt_v7(mt, b1) << 8) | a1];
-    uint32_t p2 = mt[((b0 ^ b1) << 8) | (a0 ^ a1)];
+    uint32_t p0 = M.mt[(b0 << 8) | a0];
+    uint32_t p1 = M.mt[(mt_v7(M, b1) << 8) | a1];
+    uint32_t p2 = M.mt[((b0 ^ b1) << 8) | (a0 ^ a1)];
     return (p0 ^ p1) | ((p2 ^ p0) << 8);
 }
 
-__device__ __forceinline__ uint32_t mt_gmul32(const uint8_t *mt, uint32_t a, uint32_t b) {
+__device__ __forceinline__ uint32_t mt_gmul32(const MtRef &M, uint32_t a, uint32_t b) {
     uint32_t a0 = a & 0xffff, a1 = a >> 16, b0 = b & 0xffff, b1 = b >> 16;
-    uint32_t p0 = mt_gmul16(mt, a0, b0);
-    uint32_t p1 = mt_gmul16(mt, a1, mt_p16(mt, b1));
-    uint32_t p2 = mt_gmul16(mt, a0 ^ a1, b0 ^ b1);
+    uint32_t p0 = mt_gmul16(M, a0, b0);
+    uint32_t p1 = mt_gmul16(M, a1, mt_p16(M, b1));
+    uint32_t p2 = mt_gmul16(M, a0 ^ a1, b0 ^ b1);
     return (p0 ^ p1) | ((p2 ^ p0) << 16);
 }
 
 // x * v_31 in F~_{2^32}
-__device__ __forceinline__ uint32_t mt_p32(const uint8_t *mt, uint32_t x) {
+__device__ __forceinline__ uint32_t mt_p32(const MtRef &M, uint32_t x) {
     uint32_t x0 = x & 0xffff, x1 = x >> 16;
-    return mt_p16(mt, mt_p16(mt, x1)) | (mt_p16(mt, x0 ^ x1) << 16);
+    return mt_p16(M, mt_p16(M, x1)) | (mt_p16(M, x0 ^ x1) << 16);
 }
 
-__device__ __forceinline__ u32x2 mt_gmul64(const uint8_t *mt, u32x2 a, u32x2 b) {
-    uint32_t p0 = mt_gmul32(mt, a.lo, b.lo);
-    uint32_t p1 = mt_gmul32(mt, a.hi, mt_p32(mt, b.hi));
-    uint32_t p2 = mt_gmul32(mt, a.lo ^ a.hi, b.lo ^ b.hi);
+__device__ __forceinline__ u32x2 mt_gmul64(const MtRef &M, u32x2 a, u32x2 b) {
+    uint32_t p0 = mt_gmul32(M, a.lo, b.lo);
+    uint32_t p1 = mt_gmul32(M, a.hi, mt_p32(M, b.hi));
+    uint32_t p2 = mt_gmul32(M, a.lo ^ a.hi, b.lo ^ b.hi);
     return u32x2{p0 ^ p1, p2 ^ p0};
 }
 
 // x * v_63 in F~_{2^64}
-__device__ __forceinline__ u32x2 mt_p64(const uint8_t *mt, u32x2 x) {
-    return u32x2{mt_p32(mt, mt_p32(mt, x.hi)), mt_p32(mt, x.lo ^ x.hi)};
+__device__ __forceinline__ u32x2 mt_p64(const MtRef &M, u32x2 x) {
+    return u32x2{mt_p32(M, mt_p32(M, x.hi)), mt_p32(M, x.lo ^ x.hi)};
 }
 
-__device__ __forceinline__ uint4 mt_gmul128(const uint8_t *mt, uint4 a, uint4 b) {
+__device__ __forceinline__ uint4 mt_gmul128(const MtRef &M, uint4 a, uint4 b) {
     u32x2 a0{a.x, a.y}, a1{a.z, a.w}, b0{b.x, b.y}, b1{b.z, b.w};
-    u32x2 p0 = mt_gmul64(mt, a0, b0);
-    u32x2 p1 = mt_gmul64(mt, a1, mt_p64(mt, b1));
-    u32x2 p2 = mt_gmul64(mt, u32x2{a0.lo ^ a1.lo, a0.hi ^ a1.hi}, u32x2{b0.lo ^ b1.lo, b0.hi ^ b1.hi});
+    u32x2 p0 = mt_gmul64(M, a0, b0);
+    u32x2 p1 = mt_gmul64(M, a1, mt_p64(M, b1));
+    u32x2 p2 = mt_gmul64(M, u32x2{a0.lo ^ a1.lo, a0.hi ^ a1.hi}, u32x2{b0.lo ^ b1.lo, b0.hi ^ b1.hi});
     return make_uint4(p0.lo ^ p1.lo, p0.hi ^ p1.hi, p2.lo ^ p0.lo, p2.hi ^ p0.hi);
 }
 
