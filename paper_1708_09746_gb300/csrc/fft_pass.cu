@@ -150,6 +150,107 @@ __device__ __forceinline__ void limb_subpass(uint4 *s, int g, int uf, const uint
     }
 }
 
+// Rows 0, 1, 2 of a contiguous tile (c = 0) of at least 2^8 elements.  The
+// multiplier of row r at index i is s_r(phi(i with bits 0..r cleared)), linear
+// in the index bits (Sec. 4.4), so it splits into
+//   cval[r]            the bits above the tile (the same for the whole tile),
+//   D(r, blk, h)       bits 8.. of the tile index (blk, the same for a warp) and
+//                      bits r+1..2 (h, the butterfly block inside a group of 8),
+//   delta_r(l)         bits 3..7 = the lane l (the same for every tile and warp).
+// Lane l holds the 8 elements of group (blk << 5) | l in registers, so the three
+// rows take one shared-memory round trip.  The product by cval[r] ^ D uses the
+// warp's shuffle table of that sum (the tile's table XOR the precomputed one);
+// the product by delta_r(l), an element of F~_{2^8}, is 16 byte lookups in the
+// lane's own table (byte r + 1 of word x * 32 + l).  The lane reads its group in
+// the order m ^ (l & 7), so the eight lanes of each 128-byte request hit eight
+// different 16-byte bank groups, and three conditional register swaps put the
+// elements back in index order (and out of it again before the writes).
+__device__ __forceinline__ void swap8(uint4 (&e)[8], uint32_t sig) {
+#pragma unroll
+    for (int bit = 0; bit < 3; bit++) {
+        const bool p = (sig >> bit) & 1u;
+#pragma unroll
+        for (int m = 0; m < 8; m++) {
+            if (m & (1 << bit)) continue;
+            const int n = m | (1 << bit);
+            const uint4 x = e[m], y = e[n];
+            e[m] = p ? y : x;
+            e[n] = p ? x : y;
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ uint32_t lane_mul32(const uint8_t *lt, uint32_t x) {
+    const uint32_t b0 = lt[((x & 255u) << 7) + R + 1];
+    const uint32_t b1 = lt[(((x >> 8) & 255u) << 7) + R + 1];
+    const uint32_t b2 = lt[(((x >> 16) & 255u) << 7) + R + 1];
+    const uint32_t b3 = lt[((x >> 24) << 7) + R + 1];
+    return b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+}
+
+template <int R>
+__device__ __forceinline__ uint4 low_mul128(uint4 v, const ShflTab &T, const uint8_t *lt) {
+    const uint4 p = shfl_mul128(v, T);
+    return make_uint4(p.x ^ lane_mul32<R>(lt, v.x), p.y ^ lane_mul32<R>(lt, v.y),
+                      p.z ^ lane_mul32<R>(lt, v.z), p.w ^ lane_mul32<R>(lt, v.w));
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void low_row(uint4 (&e)[8], uint32_t blk, const uint32_t *ctab,
+                                        const uint32_t *__restrict__ low_shfl, const uint8_t *lt) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 0; h < (4 >> R); h++) {
+        ShflTab T;
+        const uint32_t *dp = low_shfl + (size_t)(kLowOff[R] + blk * (4 >> R) + h) * 224 + lane;
+        const uint32_t *cp = ctab + R * 224 + lane;
+#pragma unroll
+        for (int w = 0; w < 7; w++) T.t[w] = cp[32 * w] ^ __ldg(dp + 32 * w);
+#pragma unroll
+        for (int j = 0; j < (1 << R); j++) {
+            uint4 &u = e[h * (2 << R) + j];
+            uint4 &v = e[h * (2 << R) + j + (1 << R)];
+            if (!INV) {
+                u = xor4(u, low_mul128<R>(v, T, lt));
+                v = xor4(v, u);
+            } else {
+                v = xor4(v, u);
+                u = xor4(u, low_mul128<R>(v, T, lt));
+            }
+        }
+    }
+}
+
+template <bool INV>
+__device__ __forceinline__ void low3_subpass(uint4 *s, int g, const uint32_t *ctab,
+                                             const uint32_t *__restrict__ low_shfl,
+                                             const uint32_t *lane_tab) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t sig = lane & 7;
+    const uint8_t *lt = reinterpret_cast<const uint8_t *>(lane_tab + lane);
+    const uint32_t nblk = 1u << (g - 8);
+    for (uint32_t blk = warp; blk < nblk; blk += nwarps) {
+        uint4 *grp = s + ((((blk << 5) | (uint32_t)lane)) << 3);
+        uint4 e[8];
+#pragma unroll
+        for (int m = 0; m < 8; m++) e[m] = grp[m ^ sig];
+        swap8(e, sig);
+        if (!INV) {
+            low_row<2, false>(e, blk, ctab, low_shfl, lt);
+            low_row<1, false>(e, blk, ctab, low_shfl, lt);
+            low_row<0, false>(e, blk, ctab, low_shfl, lt);
+        } else {
+            low_row<0, true>(e, blk, ctab, low_shfl, lt);
+            low_row<1, true>(e, blk, ctab, low_shfl, lt);
+            low_row<2, true>(e, blk, ctab, low_shfl, lt);
+        }
+        swap8(e, sig);
+#pragma unroll
+        for (int m = 0; m < 8; m++) grp[m ^ sig] = e[m];
+    }
+}
+
 // One lane-varying layer r of a contiguous tile (c = 0) swept in shared memory.
 template <bool INV>
 __device__ __forceinline__ void smem_layer(uint4 *s, int g, int r, const MtRef &mt, uint32_t cv,
@@ -188,14 +289,14 @@ __device__ __forceinline__ uint32_t tile_cval(const FftPassArgs &a, uint64_t tt,
 }
 
 // Starts the asynchronous copies of the byte-sliced shuffle tables of the
-// multipliers cv[r], r = uf .. g-1 (Sec. 4.4: the table of c is the XOR of
-// the tables of its four bytes) into stab[(r - uf) * 4 + byte][224].
-__device__ __forceinline__ void prefetch_tables(const FftPassArgs &a, const uint32_t *cv,
+// multipliers cv[r], r = tb .. g-1 (Sec. 4.4: the table of c is the XOR of
+// the tables of its four bytes) into stab[(r - tb) * 4 + byte][224].
+__device__ __forceinline__ void prefetch_tables(const FftPassArgs &a, int tb, const uint32_t *cv,
                                                 uint32_t *stab) {
-    const int gt = a.g - a.uf;
+    const int gt = a.g - tb;
     for (int q = threadIdx.x; q < gt * 4 * 56; q += blockDim.x) {
         const int piece = q / 56, chunk = q - piece * 56;
-        const int r = a.uf + (piece >> 2), p = piece & 3;
+        const int r = tb + (piece >> 2), p = piece & 3;
         const uint32_t byte = (cv[r] >> (8 * p)) & 255;
         cp_async16(stab + piece * 224 + chunk * 4, &a.T->shfl_m4r[p][byte][0][0] + chunk * 4);
     }
@@ -212,7 +313,10 @@ __device__ __forceinline__ void prefetch_tables(const FftPassArgs &a, const uint
 // asynchronously while the current tile is computed.
 __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int g = a.g, c = a.c, uf = a.uf, gt = g - uf;
+    const int g = a.g, c = a.c, uf = a.uf;
+    // shuffle tables of the tile's multipliers for rows tb .. g-1 (all rows
+    // when rows 0-2 run in registers with per-lane tables)
+    const int tb = a.low3 ? 0 : uf, gt = g - tb;
     // rows [uf, ul) run limb-wise (only the contiguous bottom pass: rows 3, 4)
     const int ul = (c == 0 && uf == 3 && g >= 5) ? 5 : uf;
     const uint32_t tile = 1u << (g + c);
@@ -227,7 +331,9 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     const bool from_g = a.g64 != nullptr;
     const bool pipe = !from_g;                // tiles by bulk copies
     uint8_t *mt = tail;                       // 64 KiB if needed
-    uint32_t *v7tab = reinterpret_cast<uint32_t *>(tail + 65536);  // kV7TabBytes with mt
+    // per-lane tables (v_7 and the rows 0-2 products) after the product table
+    uint32_t *lane_tab = reinterpret_cast<uint32_t *>(tail + (a.needs_mt ? 65536 : 0));
+    const uint32_t *ctab_u = ctab + (uf - tb) * 224;  // row uf's table
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const TileGeom G{c, a.k_lo, g, 4};
@@ -257,14 +363,18 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         const uint4 *src = reinterpret_cast<const uint4 *>(a.T->mul8);
         uint4 *dst = reinterpret_cast<uint4 *>(mt);
         for (int i = threadIdx.x; i < 4096; i += blockDim.x) dst[i] = __ldg(src + i);
-        v7tab_fill(v7tab, a.T->mul8);
     }
-    const MtRef M = mt_ref(mt, v7tab);
+    if (a.needs_mt || a.low3) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(&a.T->low_lane[0][0]);
+        uint4 *dst = reinterpret_cast<uint4 *>(lane_tab);
+        for (int i = threadIdx.x; i < (int)(kLaneTabBytes / 16); i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    const MtRef M = mt_ref(mt, lane_tab);
     if ((int)threadIdx.x < g && blockIdx.x < ntiles)
         cnext[threadIdx.x] = tile_cval(a, blockIdx.x & tmask, threadIdx.x);
     __syncthreads();
     if (blockIdx.x < ntiles) {
-        prefetch_tables(a, cnext, stab);
+        prefetch_tables(a, tb, cnext, stab);
         if (warp == 0 && pipe)
             tile_load_issue(G, src_of(blockIdx.x), src_tile(blockIdx.x & tmask), buf0, &bar[0], lane);
     }
@@ -314,24 +424,29 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         // the next tile's multipliers and their tables
         if ((int)threadIdx.x < g && tn < ntiles) cnext[threadIdx.x] = tile_cval(a, tn & tmask, threadIdx.x);
         __syncthreads();
-        if (tn < ntiles) prefetch_tables(a, cnext, stab);
+        if (tn < ntiles) prefetch_tables(a, tb, cnext, stab);
 
         if (a.mode != 1) {  // forward layers g_f-1 .. 0
             for (int r_hi = a.g_f - 1; r_hi >= ul; r_hi -= 3) {
                 const int r_lo = max(ul, r_hi - 2);
-                run_subpass<false>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab, a.d_shfl);
+                run_subpass<false>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab_u, a.d_shfl);
                 __syncthreads();
             }
             if (ul > uf && a.g_f > uf) {  // rows 3, 4 limb-wise
                 if (a.g_f >= 5)
-                    limb_subpass<2, false>(s, g, uf, ctab, a.d_shfl);
+                    limb_subpass<2, false>(s, g, uf, ctab_u, a.d_shfl);
                 else
-                    limb_subpass<1, false>(s, g, uf, ctab, a.d_shfl);
+                    limb_subpass<1, false>(s, g, uf, ctab_u, a.d_shfl);
                 __syncthreads();
             }
-            for (int r = min(uf, a.g_f) - 1; r >= 0; r--) {
-                smem_layer<false>(s, g, r, M, cval[r], a.d_val);
+            if (a.low3 && a.g_f >= 3) {  // rows 2, 1, 0 in registers
+                low3_subpass<false>(s, g, ctab, a.T->low_shfl[0][0], &lane_tab[0]);
                 __syncthreads();
+            } else {
+                for (int r = min(uf, a.g_f) - 1; r >= 0; r--) {
+                    smem_layer<false>(s, g, r, M, cval[r], a.d_val);
+                    __syncthreads();
+                }
             }
         }
         if (a.mode == 2) {  // pointmul with the other operand's transform
@@ -342,17 +457,22 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
             __syncthreads();
         }
         if (a.mode != 0) {  // inverse layers 0 .. g-1
-            for (int r = 0; r < min(uf, g); r++) {
-                smem_layer<true>(s, g, r, M, cval[r], a.d_val);
+            if (a.low3) {  // rows 0, 1, 2 in registers
+                low3_subpass<true>(s, g, ctab, a.T->low_shfl[0][0], &lane_tab[0]);
                 __syncthreads();
+            } else {
+                for (int r = 0; r < min(uf, g); r++) {
+                    smem_layer<true>(s, g, r, M, cval[r], a.d_val);
+                    __syncthreads();
+                }
             }
             if (ul > uf) {  // rows 3, 4 limb-wise
-                limb_subpass<2, true>(s, g, uf, ctab, a.d_shfl);
+                limb_subpass<2, true>(s, g, uf, ctab_u, a.d_shfl);
                 __syncthreads();
             }
             for (int r_lo = ul; r_lo < g; r_lo += 3) {
                 const int r_hi = min(g - 1, r_lo + 2);
-                run_subpass<true>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab, a.d_shfl);
+                run_subpass<true>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab_u, a.d_shfl);
                 __syncthreads();
             }
         }
@@ -383,11 +503,13 @@ __global__ void __launch_bounds__(256) k_pointmul_mt(const uint4 *__restrict__ A
     extern __shared__ __align__(128) unsigned char smem[];
     uint8_t *mt = smem;
     const uint4 *src = reinterpret_cast<const uint4 *>(T->mul8);
-    uint32_t *v7tab = reinterpret_cast<uint32_t *>(smem + 65536);
+    uint32_t *lane_tab = reinterpret_cast<uint32_t *>(smem + 65536);
     for (int i = threadIdx.x; i < 4096; i += blockDim.x) reinterpret_cast<uint4 *>(mt)[i] = __ldg(src + i);
-    v7tab_fill(v7tab, T->mul8);
+    const uint4 *lsrc = reinterpret_cast<const uint4 *>(&T->low_lane[0][0]);
+    for (int i = threadIdx.x; i < (int)(kLaneTabBytes / 16); i += blockDim.x)
+        reinterpret_cast<uint4 *>(lane_tab)[i] = __ldg(lsrc + i);
     __syncthreads();
-    const MtRef M = mt_ref(mt, v7tab);
+    const MtRef M = mt_ref(mt, lane_tab);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
         C[i] = mt_gmul128(M, A[i], B[i]);
@@ -475,13 +597,14 @@ int cached_pass_tables(int k_lo, int g, int uf, const uint32_t **d_val, const ui
 }
 
 // Shared memory of a pass: one or two tile buffers, the shuffle tables of the
-// tile's multipliers and their staged byte slices, the multipliers, four
-// mbarriers, then the F~_{2^8} product table and the per-lane v_7 table if
-// needed.
-size_t pass_smem(int g, int c, int uf, bool needs_mt, int nbuf) {
+// tile's multipliers (rows uf.., or all rows with low3) and their staged byte
+// slices, the multipliers, four mbarriers, then the F~_{2^8} product table if
+// needed and the per-lane tables (with the product table or low3).
+size_t pass_smem(int g, int c, int uf, bool needs_mt, int nbuf, bool low3) {
     size_t b = ((size_t)16 * nbuf) << (g + c);
-    b += (size_t)(g - uf) * 224 * 4 * 5 + 64 * 4 + 4 * 8;
-    if (needs_mt) b += 65536 + kV7TabBytes;
+    b += (size_t)(g - (low3 ? 0 : uf)) * 224 * 4 * 5 + 64 * 4 + 4 * 8;
+    if (needs_mt) b += 65536;
+    if (needs_mt || low3) b += kLaneTabBytes;
     return b;
 }
 
@@ -500,12 +623,15 @@ int make_pass(int k_lo, int g, int c, int uf, int mode, int g_f, PassTableFn src
     p->uf = uf;
     p->mode = mode;
     p->g_f = g_f;
-    p->needs_mt = (uf > 0) || mode == 2;
+    // rows 0-2 of a contiguous tile of 2^8.. elements in registers (low3);
+    // the product table for the other lane-varying rows and for pointmul
+    p->low3 = c == 0 && uf == 3 && g >= 8;
+    p->needs_mt = (uf > 0 && !p->low3) || mode == 2;
     // one buffer where two CTAs then fit an SM (no product table), or where
     // two buffers would not fit
     p->nbuf = (nbuf == 1 && !p->needs_mt) ? 1 : 2;
-    if (pass_smem(g, c, uf, p->needs_mt, p->nbuf) > kMaxPassSmem) p->nbuf = 1;
-    p->smem = pass_smem(g, c, uf, p->needs_mt, p->nbuf);
+    if (pass_smem(g, c, uf, p->needs_mt, p->nbuf, p->low3) > kMaxPassSmem) p->nbuf = 1;
+    p->smem = pass_smem(g, c, uf, p->needs_mt, p->nbuf, p->low3);
     p->threads = std::max(32, std::min(p->nbuf == 1 ? 256 : 512, (1 << (g + c)) / 2));
     return 0;
 }
@@ -614,6 +740,7 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
     a.mode = p.mode;
     a.g_f = p.g_f;
     a.needs_mt = p.needs_mt;
+    a.low3 = p.low3;
     a.M = M;
     a.status = status;
     a.count = count;
@@ -621,7 +748,7 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
     a.strideW = strideW;
     a.nbuf = p.nbuf;
     const uint64_t tiles = ((1ull << M) >> (p.g + p.c)) * (uint64_t)count;
-    const size_t smem = pass_smem(p.g, p.c, p.uf, p.needs_mt, p.nbuf);
+    const size_t smem = pass_smem(p.g, p.c, p.uf, p.needs_mt, p.nbuf, p.low3);
     // persistent CTAs: as many as are resident at once; a CTA alone on its SM
     // (shared memory too large for two) gets the full 512 threads
     int threads = p.threads;
@@ -634,7 +761,7 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
 
 void launch_pointmul_mt(const uint4 *A, const uint4 *B, uint4 *C, uint64_t n, const DevTables *T,
                         cudaStream_t s) {
-    const int smem = 65536 + (int)kV7TabBytes;
+    const int smem = 65536 + (int)kLaneTabBytes;
     ensure_smem_attr(reinterpret_cast<const void *>(k_pointmul_mt), smem);
     uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 152 * 2);
     k_pointmul_mt<<<(unsigned)std::max<uint64_t>(1, blocks), 256, smem, s>>>(A, B, C, n, T);

@@ -17,6 +17,8 @@ struct FftPassCfg {
     int mode;      // 0 forward, 1 inverse, 2 forward + pointmul + inverse
     int g_f;       // forward layers computed (mode 0/2): rows 0 .. g_f-1
     bool needs_mt; // F~_{2^8} product table in shared memory
+    bool low3;     // rows 0-2 in registers with per-lane tables (contiguous
+                   // tile of at least 2^8 elements); else product-table layers
     const uint32_t *d_val;   // per-pass multipliers d(k, prefix)
     const uint32_t *d_shfl;  // their warp-shuffle tables (rows r >= uf)
     size_t smem;
@@ -35,7 +37,7 @@ struct FftPassArgs {
     const uint32_t *d_val;
     const uint32_t *d_shfl;
     int k_lo, g, c, uf, mode, g_f;
-    bool needs_mt;
+    bool needs_mt, low3;
     int M;        // log2 of the transform length
     int *status;  // device status word (a bounded wait that ran out stores GF2X_ETIMEOUT)
     int count;    // products in the launch: product y at F + y * strideF,

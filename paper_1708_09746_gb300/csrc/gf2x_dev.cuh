@@ -22,7 +22,15 @@ struct DevTables {
     uint8_t mul8[65536];
     uint32_t shfl_basis[32][7][32];
     uint32_t shfl_m4r[4][256][7][32];
+    // Rows 0-2 of a contiguous FFT tile.  low_lane[x][l]: byte 0 = v_7 x,
+    // byte 1 + r = delta_r(l) x with delta_r(l) = s_r(phi(l << 3)), an element
+    // of F~_{2^8} (products in F~_{2^8}).  low_shfl[kLowOff[r] + blk * (4 >> r)
+    // + h]: the shuffle table of s_r(phi((blk << 8) | (h << (r + 1)))).
+    uint32_t low_lane[256][32];
+    uint32_t low_shfl[112][7][32];
 };
+
+constexpr int kLowOff[3] = {0, 64, 96};
 
 __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) {
     return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);

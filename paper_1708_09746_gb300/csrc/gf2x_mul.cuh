@@ -42,29 +42,21 @@ __device__ __forceinline__ uint4 shfl_mul128(uint4 v, const ShflTab &T) {
 }
 
 // ---- F~_{2^8} product table: mt[(c << 8) | x] = c * x ----------------------
-// The products by the constants v_7 and v_7^2 (the reductions X^2 = X + v_{W-1}
-// of every tower level end in them) come from a second table with one copy per
-// lane: word x * 32 + l holds v_7 x (byte 0) and v_7^2 x (byte 1) for lane l,
-// so the 32 lanes of a warp always read 32 different banks.  `v7` points at
-// the calling lane's byte 0 of entry 0 (table base + 4 * lane).
+// The products by the constant v_7 (the reductions X^2 = X + v_{W-1} of every
+// tower level end in them) come from a second table with one copy per lane:
+// byte 0 of word x * 32 + l is v_7 x for lane l, so the 32 lanes of a warp
+// always read 32 different banks (bytes 1..3 hold the per-lane products of the
+// lowest FFT rows, DevTables::low_lane).  `v7` points at the calling lane's
+// word of entry 0 (table base + 4 * lane).
 struct MtRef {
     const uint8_t *mt;
     const uint8_t *v7;
 };
 
-constexpr size_t kV7TabBytes = 256 * 32 * 4;
+constexpr size_t kLaneTabBytes = 256 * 32 * 4;
 
-// Fills the per-lane v_7 table (kV7TabBytes) from the global product table.
-__device__ __forceinline__ void v7tab_fill(uint32_t *dst, const uint8_t *__restrict__ mul8) {
-    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) {
-        const uint32_t x = (uint32_t)i >> 5;
-        const uint32_t y = __ldg(mul8 + (0x8000u | x));
-        dst[i] = y | ((uint32_t)__ldg(mul8 + (0x8000u | y)) << 8);
-    }
-}
-
-__device__ __forceinline__ MtRef mt_ref(const uint8_t *mt, const uint32_t *v7tab) {
-    return MtRef{mt, reinterpret_cast<const uint8_t *>(v7tab + (threadIdx.x & 31))};
+__device__ __forceinline__ MtRef mt_ref(const uint8_t *mt, const uint32_t *lane_tab) {
+    return MtRef{mt, reinterpret_cast<const uint8_t *>(lane_tab + (threadIdx.x & 31))};
 }
 
 __device__ __forceinline__ uint32_t mt_v7(const MtRef &M, uint32_t x) {
@@ -72,7 +64,7 @@ __device__ __forceinline__ uint32_t mt_v7(const MtRef &M, uint32_t x) {
 }
 
 __device__ __forceinline__ uint32_t mt_v77(const MtRef &M, uint32_t x) {
-    return M.v7[(x << 7) + 1];  // x * v_7^2
+    return mt_v7(M, mt_v7(M, x));  // x * v_7^2
 }
 
 // x * v_15 in F~_{2^16}

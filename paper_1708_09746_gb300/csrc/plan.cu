@@ -1,6 +1,7 @@
 // Product plans and the stage order of Alg. 5 (binPolyMul).
 #include <algorithm>
 #include <cstring>
+#include <stdexcept>
 
 #include "kernels.h"
 #include "plan.h"
@@ -26,6 +27,31 @@ void fill_dev_tables(DevTables *h) {
     std::memcpy(h->mul8, H.mul8, sizeof(H.mul8));
     std::memcpy(h->shfl_basis, H.shfl_basis, sizeof(H.shfl_basis));
     std::memcpy(h->shfl_m4r, H.shfl_m4r, sizeof(H.shfl_m4r));
+    // rows 0-2 of contiguous FFT tiles: s_r of index bits 3..7 (per lane) and
+    // of bits 8..11 and r+1..2 (per warp), by the linearity of s_r
+    auto s_of = [&](int r, uint32_t alpha) {
+        uint32_t v = 0;
+        for (int t = 0; t < 32; t++)
+            if ((alpha >> t) & 1) v ^= H.S[r][t];
+        return v;
+    };
+    for (int x = 0; x < 256; x++)
+        for (int l = 0; l < 32; l++) {
+            uint32_t w = H.mul8[(0x80 << 8) | x];
+            for (int r = 0; r < 3; r++) {
+                const uint32_t d = s_of(r, (uint32_t)l << 3);
+                if (d > 255) throw std::runtime_error("delta_r(l) outside F~_{2^8}");
+                w |= (uint32_t)H.mul8[(d << 8) | x] << (8 * (r + 1));
+            }
+            h->low_lane[x][l] = w;
+        }
+    for (int r = 0; r < 3; r++)
+        for (int blk = 0; blk < 16; blk++)
+            for (int hh = 0; hh < (4 >> r); hh++) {
+                uint32_t t[7][32];
+                shfl_table_of(s_of(r, ((uint32_t)blk << 8) | ((uint32_t)hh << (r + 1))), t);
+                std::memcpy(h->low_shfl[kLowOff[r] + blk * (4 >> r) + hh], t, sizeof(t));
+            }
 }
 
 void shape_of(uint64_t na_bits, uint64_t nb_bits, int *M, int *pa_log, int *pb_log) {
