@@ -106,8 +106,11 @@ __device__ __forceinline__ void bcvt_run(T *s, uint32_t tile, int a_top, int K) 
     // and step 2 applies exactly to the rows with bit jj of n clear: the run is
     // a superset-sum over the G row bits (order-free, its own inverse).
     const uint32_t r_int = (1u << G) << (a_low - K);
+    // q / S as a multiply-high: with m = ceil(2^32 / S) the quotient is exact
+    // while q * S < 2^32 (q, S < 2^16 in a tile; S = (2^K - 1) 2^s >= 3)
+    const uint32_t mS = 0xffffffffu / S + 1u;
     for (uint32_t q = threadIdx.x; q < items; q += blockDim.x) {
-        const uint32_t seg = q / S, r = q - seg * S;
+        const uint32_t seg = __umulhi(q, mS), r = q - seg * S;
         const uint32_t sb = seg * Z + r;
         if (r >= r_int) {
             T v[1 << G];
@@ -200,10 +203,13 @@ __global__ void __launch_bounds__(256) k_bcvt_class(T *f, int a_top, int K, uint
     const uint64_t r0 = BND ? 0 : r_int, nr = BND ? r_int : S - r_int;
     const uint64_t items = (n_el / Z) * nr * L;
     const uint64_t rowstep = S * L;
+    // rest / nr as a multiply-high: with m = ceil(2^64 / nr) the quotient is
+    // exact while rest * nr < 2^64
+    const uint64_t mnr = nr > 1 ? ~0ull / nr + 1ull : 0;
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < items;
          q += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t rest = q / L;
-        const uint64_t seg = rest / nr, r = r0 + (rest - seg * nr);
+        const uint64_t seg = nr > 1 ? __umul64hi(rest, mnr) : rest, r = r0 + (rest - seg * nr);
         uint32_t *const base = F + (seg * Z + r) * L + (q % L);
         if constexpr (!BND) {
             uint32_t v[1 << G];

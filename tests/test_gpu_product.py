@@ -31,7 +31,10 @@ SMALL = [(1, 1), (1, 64), (64, 1), (64, 64), (65, 63), (127, 129), (128, 128),
          (64 * 33, 64 * 31 + 5), (8191, 8193), (65536, 65536), (65536, 65535),
          (100000, 3), (131072 + 64, 131072 - 64),
          # b of 9 .. 16 words: its forward transform stops at layer 3
-         (64 * 100, 64 * 16), (64 * 100, 64 * 9), (64 * 300, 64 * 32)]
+         (64 * 100, 64 * 16), (64 * 100, 64 * 9), (64 * 300, 64 * 32),
+         # b of 2 .. 4 words under a bottom tile of 2^9 points: forward rows
+         # below 3 only, on the product table; the inverse rows 0-2 in registers
+         (64 * 300, 64 * 4), (64 * 300, 64 * 2), (64 * 200, 64 * 3 + 1)]
 
 
 @pytest.mark.parametrize("na,nb", SMALL)

@@ -69,7 +69,10 @@ def test_chrepr(p, n):
     assert got == [phi[i % p] for i in range(n)]
 
 
-@pytest.mark.parametrize("log_n,log_p", [(1, 1), (1, 0), (4, 3), (6, 6), (10, 9), (12, 12), (12, 7)])
+# bottom tiles of 2^8 .. 2^12 points run rows 0-2 in registers with per-lane
+# tables, smaller ones on the product table: both sides of the switch
+@pytest.mark.parametrize("log_n,log_p", [(1, 1), (1, 0), (4, 3), (6, 6), (7, 7), (8, 8), (9, 4),
+                                         (10, 9), (11, 11), (12, 12), (12, 7)])
 def test_fft_forward(log_n, log_p):
     n, p = 1 << log_n, 1 << log_p
     g = _rand128(400 + log_n, p)
@@ -81,7 +84,7 @@ def test_fft_forward(log_n, log_p):
     assert got == want
 
 
-@pytest.mark.parametrize("log_n", [1, 5, 10, 12])
+@pytest.mark.parametrize("log_n", [1, 5, 7, 8, 9, 10, 11, 12])
 def test_fft_inverse(log_n):
     n = 1 << log_n
     vals = _rand128(500 + log_n, n)
