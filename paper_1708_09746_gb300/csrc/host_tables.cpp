@@ -150,16 +150,21 @@ const HostTables &host_tables() {
 
 // Alg. 3 on 2^m coefficients of `scale_log`-sized blocks: y = s_K with K the
 // largest power of two <= m-1; VarSubs divides by y^(2^j) = x^E + x^e from
-// the top (E = 2^a, e = 2^(a-K), a = m-1 .. K); then BasisCvt over y (the
-// blocks of 2^K coefficients as coefficients) and over each block.
+// the top (E = 2^a, e = 2^(a-K), a = m-1 .. K); then BasisCvt over each block
+// and BasisCvt over y (the blocks of 2^K coefficients as coefficients).  The
+// last two act on disjoint index bits (below K, and K and above: the same map
+// on every block, and the same map on every position inside the blocks), so
+// they commute; Alg. 3 takes them the other way round.  Converting the blocks
+// first lets their levels share a shared-memory tile with the VarSubs levels
+// just above them.
 static void levels_rec(int m, int scale_log, LevelList &out) {
     if (m <= 1) return;
     int K = 1;
     while (2 * K <= m - 1) K *= 2;
     for (int a = m - 1; a >= K; a--)
         out.push(Level{(int8_t)(a + scale_log), (int8_t)(a - K + scale_log)});
-    levels_rec(m - K, scale_log + K, out);
     levels_rec(K, scale_log, out);
+    levels_rec(m - K, scale_log + K, out);
 }
 
 LevelList basis_cvt_levels(int m) {

@@ -280,8 +280,9 @@ __device__ __forceinline__ void div_regs(T (&v)[N]) {
 // The whole BasisCvt of M = 2 or 4 index bits at scale sc (Alg. 3 on 2^M
 // coefficients spaced 2^sc apart): a thread holds one group in registers and
 // applies its divisions, known at compile time.  For M = 4 they are
-// (x^8 + x^2), (x^4 + x) on each half, then (x^8 + x^4) and (x^2 + x) on each
-// quarter; for M = 2 the single (x^2 + x).
+// (x^8 + x^2), (x^4 + x) on each half, then (x^2 + x) and (x^8 + x^4) on each
+// quarter (the children in the library's order); for M = 2 the single
+// (x^2 + x).
 template <typename T, int M, bool INV>
 __device__ __forceinline__ void bcvt_sub(T *s, uint32_t tile, int sc) {
     constexpr int N = 1 << M;
@@ -296,11 +297,11 @@ __device__ __forceinline__ void bcvt_sub(T *s, uint32_t tile, int sc) {
         } else if constexpr (!INV) {
             div_regs<16, 8, 2, false>(v);
             div_regs<16, 4, 1, false>(v);
-            div_regs<16, 8, 4, false>(v);
             div_regs<16, 2, 1, false>(v);
+            div_regs<16, 8, 4, false>(v);
         } else {
-            div_regs<16, 2, 1, true>(v);
             div_regs<16, 8, 4, true>(v);
+            div_regs<16, 2, 1, true>(v);
             div_regs<16, 4, 1, true>(v);
             div_regs<16, 8, 2, true>(v);
         }
@@ -659,7 +660,9 @@ static void launch_bcvt_top(T *f, int h, int inverse, cudaStream_t s, int count,
 // Steps of a BasisCvt of 2^m coefficients in forward order (global index
 // bits), from the recursion of Alg. 3: a node of 2 or 4 bits is one
 // register transform; a larger node's VarSubs divisions (a, a - K) become
-// runs of at most max_g(K, a) levels, followed by its two children.
+// runs of at most max_g(K, a) levels, followed by its two children, the low
+// one (bits below K) first: the children commute, and the low one then
+// shares a tile with the VarSubs runs above it.
 struct OpList {
     static constexpr int kMax = 64;
     int n = 0;
@@ -684,7 +687,7 @@ static bool ops_rec(int m, int sc, OpList &out, const F &max_g) {
         a -= g;
         left -= g;
     }
-    return ops_rec(m - K, sc + K, out, max_g) && ops_rec(K, sc, out, max_g);
+    return ops_rec(K, sc, out, max_g) && ops_rec(m - K, sc + K, out, max_g);
 }
 
 // The divisions (logE, loge) of a step, in forward order.
@@ -694,11 +697,11 @@ static int op_levels(const BcvtOp &o, Level *lv) {
         lv[0] = Level{(int8_t)(s + 1), (int8_t)s};
         return 1;
     }
-    if (o.kind == 2) {
+    if (o.kind == 2) {  // VarSubs, then the low child, then the high one
         lv[0] = Level{(int8_t)(s + 3), (int8_t)(s + 1)};
         lv[1] = Level{(int8_t)(s + 2), (int8_t)s};
-        lv[2] = Level{(int8_t)(s + 3), (int8_t)(s + 2)};
-        lv[3] = Level{(int8_t)(s + 1), (int8_t)s};
+        lv[2] = Level{(int8_t)(s + 1), (int8_t)s};
+        lv[3] = Level{(int8_t)(s + 3), (int8_t)(s + 2)};
         return 4;
     }
     for (int i = 0; i < o.G; i++) lv[i] = Level{(int8_t)(o.a_top - i), (int8_t)(o.a_top - i - o.K)};
@@ -778,7 +781,7 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
         return g;
     };
     OpList ops;
-    bool ok = h_top ? (ops_rec(m - 16, 16, ops, max_g) && ops_rec(16, 0, ops, max_g))
+    bool ok = h_top ? (ops_rec(16, 0, ops, max_g) && ops_rec(m - 16, 16, ops, max_g))
                     : ops_rec(m, 0, ops, max_g);
     {  // the steps must expand to exactly the remaining divisions of fwd
         int q = h_top;

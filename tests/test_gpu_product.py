@@ -150,3 +150,25 @@ def test_batched_uneven():
     for p, o in zip(pairs, outs):
         want = P.mul(p[0], p[1], p[2], p[3])
         assert np.array_equal(from_dev(o, len(want)), want)
+
+
+@pytest.mark.parametrize("log_bits", [20, 24, 28])
+def test_basis_cvt_takes_grouped_passes(log_bits):
+    # Before launching, the BasisCvt schedule (register nodes, runs, class and
+    # top passes) is expanded and compared with the level list of Alg. 3; a
+    # mismatch falls back to one launch per division, which is correct but
+    # slow.  The product must take the grouped passes: a handful of launches
+    # per conversion, against 35 .. 231 divisions.
+    n = 1 << log_bits
+    a, b = W.operand_pair(log_bits, n, n)
+    G.gf2x_profile_reset()
+    G.gf2x_profile_enable(1)
+    try:
+        got = gpu_mul(a, n, b, n)
+    finally:
+        G.gf2x_profile_enable(0)
+    st = G.profile_all()
+    assert st["basis_cvt"][1] <= 2 * 8, st["basis_cvt"]
+    assert st["ibasis_cvt"][1] <= 8, st["ibasis_cvt"]
+    if log_bits <= 20:
+        assert np.array_equal(got, P.mul(a, n, b, n))
