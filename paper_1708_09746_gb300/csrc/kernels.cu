@@ -94,25 +94,83 @@ __global__ void k_bcvt_level(T *f, uint64_t n_half, int logE, int loge, int inve
 // inside each aligned 16-element block).
 __device__ __forceinline__ uint32_t sw(uint32_t x) { return x ^ ((x >> 4) & 15u); }
 
-template <typename T, int G, int RM, bool INV>
-__device__ __forceinline__ void bcvt_run(T *s, uint32_t tile, int a_top, int K) {
-    const int a_low = a_top - G + 1;
-    const uint32_t S = ((1u << K) - 1) << (a_low - K);
+// Rows of one class for a run of G levels with step K: ceil(2^(G+K) / (2^K - 1)).
+__host__ __device__ constexpr int run_rows(int G, int K) {
+    return (int)((((1u << (G + K)) + (1u << K) - 2) / ((1u << K) - 1)));
+}
+
+// K and G are known at compile time (bcvt_run_k).  All positions of a
+// class r are multiples of e_low = 2^(a_low - K) plus r mod e_low, and E, e
+// and the segment sizes are multiples of e_low, so the step conditions of a
+// row depend only on r_hi = r >> (a_low - K); on a boundary class
+// (r_hi < 2^G) they are evaluated here at compile time for each r_hi:
+// row n sits at o = (r_hi + n (2^K - 1)) mod 2^(jj + K + 1) in units of
+// e_low, with E = 2^(jj + K) and e = 2^jj.
+template <int K, int G, int RH>
+__host__ __device__ constexpr bool bnd_valid(int n) {
+    return RH + n * ((1 << K) - 1) < (1 << (K + G));
+}
+
+template <int K, int RH, bool INV>
+__host__ __device__ constexpr bool bnd_act(int jj, int st, int n) {
+    const int o = (RH + n * ((1 << K) - 1)) & ((2 << (jj + K)) - 1);
+    const int E = 1 << (jj + K), e = 1 << jj;
+    const bool step1 = (st == 0) != INV;
+    return step1 ? (o >= E && o - E < e) : (o >= e && o - e < E - e);
+}
+
+template <typename T, int K, int G, int RH, bool INV>
+__device__ __forceinline__ void bnd_class(T *s, uint32_t sb, uint32_t S) {
+    constexpr int RM = run_rows(G, K);
+    T v[RM];
+#pragma unroll
+    for (int n = 0; n < RM; n++)
+        if (bnd_valid<K, G, RH>(n)) v[n] = s[sw(sb + n * S)];
+#pragma unroll
+    for (int it = 0; it < G; it++) {
+        const int jj = INV ? it : G - 1 - it;
+#pragma unroll
+        for (int st = 0; st < 2; st++)
+#pragma unroll
+            for (int n = 0; n + (1 << jj) < RM; n++)
+                if (bnd_valid<K, G, RH>(n) && bnd_act<K, RH, INV>(jj, st, n))
+                    v[n] = xr(v[n], v[n + (1 << jj)]);
+    }
+#pragma unroll
+    for (int n = 0; n < RM; n++)
+        if (bnd_valid<K, G, RH>(n)) s[sw(sb + n * S)] = v[n];
+}
+
+template <typename T, int K, int G, bool INV, int RH = 0>
+__device__ __forceinline__ void bnd_dispatch(T *s, uint32_t sb, uint32_t S, uint32_t rh) {
+    if constexpr (RH < (1 << G)) {
+        if (rh == RH) {
+            bnd_class<T, K, G, RH, INV>(s, sb, S);
+            return;
+        }
+        bnd_dispatch<T, K, G, INV, RH + 1>(s, sb, S, rh);
+    }
+}
+
+template <typename T, int K, int G, bool INV>
+__device__ __forceinline__ void bcvt_run_k(T *s, uint32_t tile, int a_top) {
+    const int a_low = a_top - G + 1, sh = a_low - K;
+    const uint32_t S = ((1u << K) - 1) << sh;
     const uint32_t Z = 1u << (a_top + 1);
     const uint32_t items = (tile >> (a_top + 1)) * S;
-    // Classes r >= 2^G e_low (e_low = 2^(a_low - K)) are interior: writing
-    // r + n S = n 2^a_low + (r - n e_low), row n sits at (n mod 2^(jj+1))
-    // 2^a_low + (r - n e_low) in its level segment, so step 1 never applies
-    // and step 2 applies exactly to the rows with bit jj of n clear: the run is
-    // a superset-sum over the G row bits (order-free, its own inverse).
-    const uint32_t r_int = (1u << G) << (a_low - K);
+    // Classes r >= 2^G e_low are interior: writing r + n S = n 2^a_low +
+    // (r - n e_low), row n sits at (n mod 2^(jj+1)) 2^a_low + (r - n e_low) in
+    // its level segment, so step 1 never applies and step 2 applies exactly to
+    // the rows with bit jj of n clear: the run is a superset-sum over the G row
+    // bits (order-free, its own inverse).
+    const uint32_t r_int = (1u << G) << sh;
     // q / S as a multiply-high: with m = ceil(2^32 / S) the quotient is exact
-    // while q * S < 2^32 (q, S < 2^16 in a tile; S = (2^K - 1) 2^s >= 3)
+    // while q * S < 2^32 (q, S < 2^16 in a tile; S = (2^K - 1) 2^sh >= 3)
     const uint32_t mS = 0xffffffffu / S + 1u;
     for (uint32_t q = threadIdx.x; q < items; q += blockDim.x) {
         const uint32_t seg = __umulhi(q, mS), r = q - seg * S;
         const uint32_t sb = seg * Z + r;
-        if (r >= r_int) {
+        if (r >= r_int) {  // interior: superset-sum over the G row bits
             T v[1 << G];
 #pragma unroll
             for (int n = 0; n < (1 << G); n++) v[n] = s[sw(sb + n * S)];
@@ -123,66 +181,33 @@ __device__ __forceinline__ void bcvt_run(T *s, uint32_t tile, int a_top, int K) 
                     if (!((n >> jj) & 1)) v[n] = xr(v[n], v[n + (1 << jj)]);
 #pragma unroll
             for (int n = 0; n < (1 << G); n++) s[sw(sb + n * S)] = v[n];
-            continue;
+        } else {
+            bnd_dispatch<T, K, G, INV>(s, sb, S, r >> sh);
         }
-        T v[RM];
-        uint32_t valid = 0;  // bit n: row n lies inside the segment
-#pragma unroll
-        for (int n = 0; n < RM; n++) {
-            if (r + (uint32_t)n * S < Z) {
-                valid |= 1u << n;
-                v[n] = s[sw(sb + n * S)];
-            } else {
-                memset(&v[n], 0, sizeof(T));
-            }
-        }
-#pragma unroll
-        for (int it = 0; it < G; it++) {
-            const int jj = INV ? it : G - 1 - it;  // row distance 2^jj
-            const int a = a_low + jj;
-            const uint32_t E = 1u << a, e = 1u << (a - K), msk = 2 * E - 1;
-#pragma unroll
-            for (int st = 0; st < 2; st++) {
-                const bool step1 = (st == 0) != INV;  // forward: step 1 then 2
-#pragma unroll
-                for (int n = 0; n + (1 << jj) < RM; n++) {
-                    // a receiver's partner lies in the same level segment,
-                    // so a valid receiver always has a valid source
-                    const uint32_t o = (r + (uint32_t)n * S) & msk;
-                    const bool act = ((valid >> n) & 1u) && (step1 ? (o - E < e) : (o - e < E - e));
-                    if (act) v[n] = xr(v[n], v[n + (1 << jj)]);
-                }
-            }
-        }
-#pragma unroll
-        for (int n = 0; n < RM; n++)
-            if ((valid >> n) & 1u) s[sw(sb + n * S)] = v[n];
     }
-}
-
-// Rows of one class for a run of G levels with step K: ceil(2^(G+K) / (2^K - 1)).
-__host__ __device__ constexpr int run_rows(int G, int K) {
-    return (int)((((1u << (G + K)) + (1u << K) - 2) / ((1u << K) - 1)));
 }
 
 template <typename T, bool INV>
 __device__ __forceinline__ void bcvt_run_any(T *s, uint32_t tile, int a_top, int K, int G) {
-    switch (G) {
-        case 1: bcvt_run<T, 1, 4, INV>(s, tile, a_top, K); break;
-        case 2: bcvt_run<T, 2, 6, INV>(s, tile, a_top, K); break;
-        case 3:
-            if constexpr (sizeof(T) == 8)
-                bcvt_run<T, 3, 10, INV>(s, tile, a_top, K);
-            else
-                bcvt_run<T, 3, 9, INV>(s, tile, a_top, K);
-            break;
-        default: break;
+    // the (K, G) pairs of tile runs (bcvt_tile_run_ok on the host)
+    switch (K * 8 + G) {
+        case 2 * 8 + 1: bcvt_run_k<T, 2, 1, INV>(s, tile, a_top); return;
+        case 4 * 8 + 1: bcvt_run_k<T, 4, 1, INV>(s, tile, a_top); return;
+        case 4 * 8 + 2: bcvt_run_k<T, 4, 2, INV>(s, tile, a_top); return;
+        case 8 * 8 + 1: bcvt_run_k<T, 8, 1, INV>(s, tile, a_top); return;
+        case 8 * 8 + 2: bcvt_run_k<T, 8, 2, INV>(s, tile, a_top); return;
+        case 8 * 8 + 3: bcvt_run_k<T, 8, 3, INV>(s, tile, a_top); return;
+        default: return;
     }
+}
+
+static bool bcvt_tile_run_ok(int K, int G) {
+    return (K == 2 && G == 1) || (K == 4 && G >= 1 && G <= 2) || (K == 8 && G >= 1 && G <= 3);
 }
 
 // A run of G divisions (a, a - K), a = a_top .. a_top - G + 1, as one
 // streaming pass over the whole array (runs too wide for a shared-memory
-// tile: K >= 8).  The classes {r + n S} of bcvt_run are taken straight from
+// tile: K >= 8).  The classes {r + n S} of bcvt_run_k are taken straight from
 // global memory, one 32-bit limb of one class per thread (the divisions act
 // bitwise); consecutive threads take consecutive (class, limb) pairs, so every
 // row is read and written in full 128-byte lines.  Interior classes
@@ -704,8 +729,9 @@ static int op_levels(const BcvtOp &o, Level *lv) {
         lv[3] = Level{(int8_t)(s + 3), (int8_t)(s + 2)};
         return 4;
     }
-    for (int i = 0; i < o.G; i++) lv[i] = Level{(int8_t)(o.a_top - i), (int8_t)(o.a_top - i - o.K)};
-    return o.G;
+    const int g = std::min<int>(o.G, 4);  // runs have at most 4 levels
+    for (int i = 0; i < g; i++) lv[i] = Level{(int8_t)(o.a_top - i), (int8_t)(o.a_top - i - o.K)};
+    return g;
 }
 
 static void op_range(const BcvtOp &o, int *lo, int *hi) {
@@ -786,8 +812,11 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
     {  // the steps must expand to exactly the remaining divisions of fwd
         int q = h_top;
         for (int i = 0; ok && i < ops.n; i++) {
+            const BcvtOp &o = ops.v[i];
+            // tile runs need a compiled (K, G) variant
+            ok = o.kind != 0 || streamed(o) || bcvt_tile_run_ok(o.K, o.G);
             Level lv[4];
-            const int k = op_levels(ops.v[i], lv);
+            const int k = op_levels(o, lv);
             for (int t = 0; ok && t < k; t++, q++)
                 ok = q < fwd.n && fwd.v[q].logE == lv[t].logE && fwd.v[q].loge == lv[t].loge;
         }
