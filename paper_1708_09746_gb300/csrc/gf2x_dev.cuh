@@ -18,7 +18,6 @@ struct u32x2 {
 struct DevTables {
     uint32_t S[32][32];
     uint4 chr_in[8][256];
-    uint4 chr_out[16][256];
     uint8_t mul8[65536];
     uint32_t shfl_basis[32][7][32];
     uint32_t shfl_m4r[4][256][7][32];
@@ -28,6 +27,10 @@ struct DevTables {
     // + h]: the shuffle table of s_r(phi((blk << 8) | (h << (r + 1)))).
     uint32_t low_lane[256][32];
     uint32_t low_shfl[112][7][32];
+    // changeRepr^-1 as warp-shuffle tables: psi_shfl[o][q][w][l] = word o of
+    // psi(e), e = the element whose word q holds l << 5w (w < 6) or
+    // (l & 3) << 30 (w = 6) and is zero elsewhere.
+    uint32_t psi_shfl[4][4][7][32];
 };
 
 constexpr int kLowOff[3] = {0, 64, 96};

@@ -544,53 +544,89 @@ __global__ void __launch_bounds__(256) k_chrepr_stage(const uint64_t *__restrict
 // ---------------------------------------------------------------------------
 // changeRepr^-1 and InterleavedCombine (Sec. 2.1): psi(F[j]) is a polynomial
 // of degree < 128 in z; z -> x and y -> x^64 add its high word into the next
-// output word.
-__device__ __forceinline__ uint4 psi(const uint4 *__restrict__ tab, uint4 e) {
-    uint4 acc = make_uint4(0, 0, 0, 0);
-    const uint32_t wv[4] = {e.x, e.y, e.z, e.w};
-#pragma unroll
-    for (int q = 0; q < 4; q++)
-#pragma unroll
-        for (int b = 0; b < 4; b++) acc = xor4(acc, tab[(4 * q + b) * 256 + ((wv[q] >> (8 * b)) & 255)]);
-    return acc;
-}
+// output word.  psi is F_2-linear, so word o of psi(x) is the XOR over the 28
+// windows of x (seven per input word q, as in shfl_mul32) of the table entry
+// psi_shfl[o][q][w][window value]; lane l holds entry l of each window's table
+// in a register and a window lookup is one shuffle.  A warp takes chunks of
+// 32 K consecutive elements (lane l: elements l, l + 32, ...) and writes the
+// 32 K - 1 output words that need only those elements; chunks overlap by one
+// element.
+constexpr int kCombineK = 8;
 
-// Each element's psi is computed once, with the 8-bit tables (64 KiB) in
-// shared memory: output word j is the low half of psi(F[j]) XOR the high half
-// of psi(F[j-1]), which the previous lane holds (lane 0 recomputes it).  Whole
-// warps walk the words so that every lane takes part in the shuffles.
 __global__ void __launch_bounds__(256) k_ichrepr_combine(const uint4 *__restrict__ F, uint64_t n,
                                                          uint64_t stride, OutputDesc one,
                                                          const OutputDesc *__restrict__ many,
                                                          const DevTables *__restrict__ T,
                                                          uint64_t j_begin, uint64_t j_end) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint4 *tab = reinterpret_cast<uint4 *>(smem_raw);
-    const uint4 *src = &T->chr_out[0][0];
-    for (int i = threadIdx.x; i < 16 * 256; i += blockDim.x) tab[i] = __ldg(src + i);
+    __shared__ __align__(16) uint32_t tab[4 * 4 * 7 * 32];
+    const uint4 *src = reinterpret_cast<const uint4 *>(&T->psi_shfl[0][0][0][0]);
+    for (int i = threadIdx.x; i < 4 * 4 * 7 * 32 / 4; i += blockDim.x)
+        reinterpret_cast<uint4 *>(tab)[i] = __ldg(src + i);
     __syncthreads();
     const OutputDesc d = many ? many[blockIdx.y] : one;
     F += blockIdx.y * stride;
     const int lane = threadIdx.x & 31;
     const uint64_t j_stop = j_end < d.words ? j_end : d.words;  // words [j_begin, j_stop)
-    for (uint64_t j0 = j_begin + blockIdx.x * (uint64_t)blockDim.x; j0 < j_stop;
-         j0 += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t j = j0 + threadIdx.x;
-        uint4 c = make_uint4(0, 0, 0, 0);
-        if (j < n && j < j_stop) c = psi(tab, F[j]);
-        uint32_t hz = __shfl_up_sync(0xffffffffu, c.z, 1), hw = __shfl_up_sync(0xffffffffu, c.w, 1);
-        if (lane == 0) {
-            hz = hw = 0;
-            if (j >= 1 && j - 1 < n && j < j_stop) {
-                const uint4 p = psi(tab, F[j - 1]);
-                hz = p.z;
-                hw = p.w;
+    if (j_stop <= j_begin) return;
+    constexpr uint64_t per = 32 * kCombineK - 1;  // output words per chunk
+    const uint64_t chunks = (j_stop - j_begin + per - 1) / per;
+    const uint64_t wpb = blockDim.x >> 5;
+    for (uint64_t ch = blockIdx.x * wpb + (threadIdx.x >> 5); ch < chunks; ch += gridDim.x * wpb) {
+        // element t = 32 k + lane of the chunk is index s0 - 1 + t; output
+        // word s0 - 1 + t (t >= 1) is lo(psi(element t)) ^ hi(psi(element t - 1))
+        const uint64_t s0 = j_begin + ch * per;
+        uint4 e[kCombineK];
+#pragma unroll
+        for (int k = 0; k < kCombineK; k++) {
+            const uint64_t t = 32 * k + lane;
+            e[k] = make_uint4(0, 0, 0, 0);
+            if (s0 + t >= 1 && s0 + t - 1 < n) e[k] = F[s0 + t - 1];
+        }
+        // one output word of psi at a time, so that only its 28 table
+        // registers are live (the word index is kept out of register names)
+        uint32_t r[kCombineK][4];
+#pragma unroll 1
+        for (int o = 0; o < 4; o++) {
+            uint32_t tb[28];
+#pragma unroll
+            for (int qw = 0; qw < 28; qw++) tb[qw] = tab[(o * 28 + qw) * 32 + lane];
+#pragma unroll
+            for (int k = 0; k < kCombineK; k++) {
+                uint32_t wv[4] = {e[k].x, e[k].y, e[k].z, e[k].w};
+                // keep the window shifts inside the loop over o (hoisting
+                // them would hold 28 K values in registers)
+#pragma unroll
+                for (int q = 0; q < 4; q++) asm volatile("" : "+r"(wv[q]));
+                uint32_t acc = 0;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+#pragma unroll
+                    for (int w = 0; w < 6; w++) acc ^= __shfl_sync(0xffffffffu, tb[q * 7 + w], wv[q] >> (5 * w));
+                    acc ^= __shfl_sync(0xffffffffu, tb[q * 7 + 6], wv[q] >> 30);
+                }
+#pragma unroll
+                for (int oo = 0; oo < 4; oo++) r[k][oo] = o == oo ? acc : r[k][oo];
             }
         }
-        if (j < j_stop) {
-            uint64_t v = ((uint64_t)c.x | ((uint64_t)c.y << 32)) ^ ((uint64_t)hz | ((uint64_t)hw << 32));
-            if (j == d.words - 1) v &= d.mask;
-            d.out[j] = v;
+#pragma unroll
+        for (int k = 0; k < kCombineK; k++) {
+            uint32_t hz = __shfl_up_sync(0xffffffffu, r[k][2], 1);
+            uint32_t hw = __shfl_up_sync(0xffffffffu, r[k][3], 1);
+            if (k > 0) {  // lane 0: the last element of the previous row
+                const uint32_t pz = __shfl_sync(0xffffffffu, r[k > 0 ? k - 1 : 0][2], 31);
+                const uint32_t pw = __shfl_sync(0xffffffffu, r[k > 0 ? k - 1 : 0][3], 31);
+                if (lane == 0) {
+                    hz = pz;
+                    hw = pw;
+                }
+            }
+            const uint64_t t = 32 * k + lane, j = s0 + t - 1;
+            if (t >= 1 && j < j_stop) {
+                uint64_t v = ((uint64_t)r[k][0] | ((uint64_t)r[k][1] << 32)) ^
+                             ((uint64_t)hz | ((uint64_t)hw << 32));
+                if (j == d.words - 1) v &= d.mask;
+                d.out[j] = v;
+            }
         }
     }
 }
@@ -906,7 +942,6 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
 }
 
 void prepare_bcvt_attributes() {
-    ensure_smem_attr(reinterpret_cast<const void *>(k_ichrepr_combine), 65536);
     ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint64_t, false>),
                      (int)(sizeof(uint64_t) << tile_log_for<uint64_t>()));
     ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint4, false>),
@@ -937,13 +972,13 @@ void launch_ichrepr_combine(const uint4 *F, uint64_t n, uint64_t stride, const O
                             const OutputDesc *many, int count, uint64_t max_words,
                             const DevTables *T, cudaStream_t s, uint64_t j_begin,
                             uint64_t j_end) {
-    ensure_smem_attr(reinterpret_cast<const void *>(k_ichrepr_combine), 65536);
-    // a few resident CTAs per SM, each loading the 64 KiB of tables once
-    const uint64_t per = std::max<uint64_t>(1, (uint64_t)num_sms() * 3 / (uint64_t)std::max(count, 1));
+    // a few resident CTAs per SM, each loading the 14 KiB of tables once; a
+    // warp takes chunks of 32 kCombineK - 1 output words
+    const uint64_t per = std::max<uint64_t>(1, (uint64_t)num_sms() * 4 / (uint64_t)std::max(count, 1));
     const uint64_t span = std::min(j_end, max_words) > j_begin ? std::min(j_end, max_words) - j_begin : 0;
-    const uint64_t need = (span + 255) / 256;
+    const uint64_t need = (span + 8 * (32 * kCombineK - 1) - 1) / (8 * (32 * kCombineK - 1));
     dim3 grid((unsigned)std::max<uint64_t>(1, std::min(need, per)), count);
-    k_ichrepr_combine<<<grid, 256, 65536, s>>>(F, n, stride, one, many, T, j_begin, j_end);
+    k_ichrepr_combine<<<grid, 256, 0, s>>>(F, n, stride, one, many, T, j_begin, j_end);
 }
 
 }  // namespace gf2x

@@ -18,12 +18,6 @@ void fill_dev_tables(DevTables *h) {
             h->chr_in[p][v] = make_uint4((uint32_t)x.lo, (uint32_t)(x.lo >> 32), (uint32_t)x.hi,
                                          (uint32_t)(x.hi >> 32));
         }
-    for (int p = 0; p < 16; p++)
-        for (int v = 0; v < 256; v++) {
-            const u128 &x = H.chr_out[p][v];
-            h->chr_out[p][v] = make_uint4((uint32_t)x.lo, (uint32_t)(x.lo >> 32), (uint32_t)x.hi,
-                                          (uint32_t)(x.hi >> 32));
-        }
     std::memcpy(h->mul8, H.mul8, sizeof(H.mul8));
     std::memcpy(h->shfl_basis, H.shfl_basis, sizeof(H.shfl_basis));
     std::memcpy(h->shfl_m4r, H.shfl_m4r, sizeof(H.shfl_m4r));
@@ -45,6 +39,21 @@ void fill_dev_tables(DevTables *h) {
             }
             h->low_lane[x][l] = w;
         }
+    // psi tables for the shuffle form of changeRepr^-1 (psi is F_2-linear)
+    for (int q = 0; q < 4; q++)
+        for (int w = 0; w < 7; w++)
+            for (int l = 0; l < 32; l++) {
+                const uint32_t word = w < 6 ? (uint32_t)l << (5 * w) : (uint32_t)(l & 3) << 30;
+                u128 acc{0, 0};
+                for (int b = 0; b < 4; b++) {
+                    const u128 &t = H.chr_out[4 * q + b][(word >> (8 * b)) & 255];
+                    acc.lo ^= t.lo;
+                    acc.hi ^= t.hi;
+                }
+                const uint32_t o4[4] = {(uint32_t)acc.lo, (uint32_t)(acc.lo >> 32), (uint32_t)acc.hi,
+                                        (uint32_t)(acc.hi >> 32)};
+                for (int o = 0; o < 4; o++) h->psi_shfl[o][q][w][l] = o4[o];
+            }
     for (int r = 0; r < 3; r++)
         for (int blk = 0; blk < 16; blk++)
             for (int hh = 0; hh < (4 >> r); hh++) {
