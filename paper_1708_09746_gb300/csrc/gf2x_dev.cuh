@@ -31,6 +31,10 @@ struct DevTables {
     // psi(e), e = the element whose word q holds l << 5w (w < 6) or
     // (l & 3) << 30 (w = 6) and is zero elsewhere.
     uint32_t psi_shfl[4][4][7][32];
+    // changeRepr the same way: phi_shfl[o][q][w][l] = word o of phi(b), b =
+    // the 64-bit block whose 32-bit half q holds l << 5w (w < 6) or
+    // (l & 3) << 30 (w = 6) and is zero elsewhere.
+    uint32_t phi_shfl[4][2][7][32];
 };
 
 constexpr int kLowOff[3] = {0, 64, 96};

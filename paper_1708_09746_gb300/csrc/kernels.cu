@@ -518,26 +518,65 @@ __global__ void k_chrepr(const uint64_t *__restrict__ g, uint64_t pmask, uint4 *
 }
 
 // changeRepr of `count` operands ahead of their first strided FFT pass:
-// F[i] = phi(g[i]) for i < P (product y at g + y * strideW, F + y * strideF),
-// phi by the 8-bit tables held in shared memory (32 KiB per CTA).
+// F[i] = phi(g[i]) for i < P (product y at g + y * strideW, F + y * strideF).
+// phi is F_2-linear: word o of phi(b) is the XOR over the 14 five-bit windows
+// of the block b (seven per 32-bit half) of a table entry that lane `window`
+// holds in a register, one shuffle per window.  A warp takes chunks of 256
+// consecutive blocks (8 per lane), one output word of phi at a time.
+constexpr int kChreprK = 8;
+
 __global__ void __launch_bounds__(256) k_chrepr_stage(const uint64_t *__restrict__ g, uint64_t P,
                                                       uint64_t strideW, uint4 *__restrict__ F,
                                                       uint64_t strideF,
                                                       const DevTables *__restrict__ T) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint4 *tab = reinterpret_cast<uint4 *>(smem_raw);
-    const uint4 *src = &T->chr_in[0][0];
-    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) tab[i] = __ldg(src + i);
+    __shared__ __align__(16) uint32_t tab[4 * 2 * 7 * 32];
+    const uint4 *src = reinterpret_cast<const uint4 *>(&T->phi_shfl[0][0][0][0]);
+    for (int i = threadIdx.x; i < 4 * 2 * 7 * 32 / 4; i += blockDim.x)
+        reinterpret_cast<uint4 *>(tab)[i] = __ldg(src + i);
     __syncthreads();
     g += blockIdx.y * strideW;
     F += blockIdx.y * strideF;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < P;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t w = g[i];
-        uint4 acc = make_uint4(0, 0, 0, 0);
+    const int lane = threadIdx.x & 31;
+    constexpr uint64_t per = 32 * kChreprK;
+    const uint64_t chunks = (P + per - 1) / per;
+    const uint64_t wpb = blockDim.x >> 5;
+    for (uint64_t ch = blockIdx.x * wpb + (threadIdx.x >> 5); ch < chunks; ch += gridDim.x * wpb) {
+        const uint64_t i0 = ch * per + lane;
+        uint32_t b[kChreprK][2];
 #pragma unroll
-        for (int p = 0; p < 8; p++) acc = xor4(acc, tab[p * 256 + ((w >> (8 * p)) & 255)]);
-        F[i] = acc;
+        for (int k = 0; k < kChreprK; k++) {
+            const uint64_t i = i0 + 32 * k;
+            const uint64_t w = i < P ? g[i] : 0;
+            b[k][0] = (uint32_t)w;
+            b[k][1] = (uint32_t)(w >> 32);
+        }
+        uint32_t r[kChreprK][4];
+#pragma unroll 1
+        for (int o = 0; o < 4; o++) {
+            uint32_t tb[14];
+#pragma unroll
+            for (int qw = 0; qw < 14; qw++) tb[qw] = tab[(o * 14 + qw) * 32 + lane];
+#pragma unroll
+            for (int k = 0; k < kChreprK; k++) {
+                uint32_t wv[2] = {b[k][0], b[k][1]};
+                // keep the window shifts inside the loop over o
+                asm volatile("" : "+r"(wv[0]), "+r"(wv[1]));
+                uint32_t acc = 0;
+#pragma unroll
+                for (int q = 0; q < 2; q++) {
+#pragma unroll
+                    for (int w = 0; w < 6; w++) acc ^= __shfl_sync(0xffffffffu, tb[q * 7 + w], wv[q] >> (5 * w));
+                    acc ^= __shfl_sync(0xffffffffu, tb[q * 7 + 6], wv[q] >> 30);
+                }
+#pragma unroll
+                for (int oo = 0; oo < 4; oo++) r[k][oo] = o == oo ? acc : r[k][oo];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kChreprK; k++) {
+            const uint64_t i = i0 + 32 * k;
+            if (i < P) F[i] = make_uint4(r[k][0], r[k][1], r[k][2], r[k][3]);
+        }
     }
 }
 
@@ -958,9 +997,11 @@ template uint64_t run_basis_cvt<uint4>(uint4 *, int, const LevelList &, int, cud
 
 void launch_chrepr_stage(const uint64_t *g, uint64_t P, uint64_t strideW, uint4 *F,
                          uint64_t strideF, int count, const DevTables *T, cudaStream_t s) {
+    // a warp takes chunks of 32 kChreprK blocks
     const uint64_t per = std::max<uint64_t>(1, (uint64_t)num_sms() * 4 / (uint64_t)std::max(count, 1));
-    dim3 grid((unsigned)std::max<uint64_t>(1, std::min<uint64_t>((P + 255) / 256, per)), count);
-    k_chrepr_stage<<<grid, 256, 32768, s>>>(g, P, strideW, F, strideF, T);
+    const uint64_t need = (P + 8 * 32 * kChreprK - 1) / (8 * 32 * kChreprK);
+    dim3 grid((unsigned)std::max<uint64_t>(1, std::min<uint64_t>(need, per)), count);
+    k_chrepr_stage<<<grid, 256, 0, s>>>(g, P, strideW, F, strideF, T);
 }
 
 void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const DevTables *T,

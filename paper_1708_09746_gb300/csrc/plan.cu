@@ -39,6 +39,21 @@ void fill_dev_tables(DevTables *h) {
             }
             h->low_lane[x][l] = w;
         }
+    // phi tables for the shuffle form of changeRepr (phi is F_2-linear)
+    for (int q = 0; q < 2; q++)
+        for (int w = 0; w < 7; w++)
+            for (int l = 0; l < 32; l++) {
+                const uint32_t word = w < 6 ? (uint32_t)l << (5 * w) : (uint32_t)(l & 3) << 30;
+                u128 acc{0, 0};
+                for (int b = 0; b < 4; b++) {
+                    const u128 &t = H.chr_in[4 * q + b][(word >> (8 * b)) & 255];
+                    acc.lo ^= t.lo;
+                    acc.hi ^= t.hi;
+                }
+                const uint32_t o4[4] = {(uint32_t)acc.lo, (uint32_t)(acc.lo >> 32), (uint32_t)acc.hi,
+                                        (uint32_t)(acc.hi >> 32)};
+                for (int o = 0; o < 4; o++) h->phi_shfl[o][q][w][l] = o4[o];
+            }
     // psi tables for the shuffle form of changeRepr^-1 (psi is F_2-linear)
     for (int q = 0; q < 4; q++)
         for (int w = 0; w < 7; w++)
