@@ -24,8 +24,10 @@ product) on the host cores on a bounded sample of the same workload, scaled to
 ms per product.
 """
 import argparse
+import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import time
@@ -247,13 +249,12 @@ def fft_work(na, nb):
 
 
 def fft_hbm_bytes(N, M, la, lb, depth=7):
-    """Bytes the FFT stages of one product move at least: changeRepr reading
-    the P 8-byte blocks and writing P elements (when a strided pass follows),
-    each pass a tile in and a tile out (the first strided pass reading only
-    the P staged elements, a lone bottom pass the P blocks), the fused pass
-    also reading the other transform.  Passes: layers 12 .. log2 P (forward)
-    or M (inverse) in strided passes of at most `depth` layers, then the
-    4096-element bottom pass."""
+    """Bytes the FFT passes (k_fft_pass) of one product move at least: each
+    pass a tile in and a tile out (the first strided pass reading only the P
+    elements changeRepr staged, a lone bottom pass the P blocks), the fused
+    pass also reading the other transform.  Passes: layers 12 .. log2 P
+    (forward) or M (inverse) in strided passes of at most `depth` layers,
+    then the 4096-element bottom pass."""
     def strided(layers):
         return max(0, -(-(layers - 12) // depth))
     b = 0
@@ -261,7 +262,6 @@ def fft_hbm_bytes(N, M, la, lb, depth=7):
         P = 1 << L
         s = strided(L)
         if s:
-            b += 24 * P                              # changeRepr: blocks in, elements out
             b += 16 * P + 16 * N                     # first strided pass
             b += (s - 1) * 32 * N + 32 * N           # other strided passes, bottom pass
         else:
@@ -269,6 +269,34 @@ def fft_hbm_bytes(N, M, la, lb, depth=7):
     b += 16 * N                                      # fused pass reads FA
     b += strided(M) * 32 * N                         # inverse top passes
     return b
+
+
+FFT_KERNEL_SOURCES = ("fft_pass.cu", "fft_pass.h", "gf2x_mul.cuh", "gf2x_dev.cuh", "tma.cuh")
+FFT_PROFILE = os.path.join(ROOT, "profiles", "k_fft_pass_2^28.md")
+
+
+def fft_sources_sha256():
+    """sha256 over the sources of k_fft_pass, in a fixed order."""
+    h = hashlib.sha256()
+    for name in FFT_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1708_09746_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def fft_traffic_per_launch():
+    """DRAM bytes (read + write) per k_fft_pass launch from the committed ncu
+    summary, if it was taken on the current kernel sources; else None."""
+    try:
+        text = open(FFT_PROFILE).read()
+    except OSError:
+        return None
+    mb = re.search(r"^traffic_bytes_per_launch: (\d+)$", text, re.M)
+    mh = re.search(r"^kernel_sources_sha256: ([0-9a-f]{64})$", text, re.M)
+    if not mb or not mh or mh.group(1) != fft_sources_sha256():
+        return None
+    return {"bytes": int(mb.group(1)), "source": "profiles/k_fft_pass_2^28.md (ncu, sources sha256 %s)"
+            % mh.group(1)[:12]}
 
 
 def measure_sizes(G, torch, W, dev, stream, flush):
@@ -505,7 +533,7 @@ def run_ours(args):
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     # the dominant kernel: k_fft_pass runs every FFT stage
-    fft_stages = ["chrepr_fft_a", "chrepr_fft_b", "fft_pointmul_ifft_bottom", "ifft_top"]
+    fft_stages = ["fft_a", "fft_b", "fft_pointmul_ifft_bottom", "ifft_top"]
     fft_ms = sum(stages[k][0] for k in fft_stages) / args.steps
     fft_launches = sum(stages[k][1] for k in fft_stages) / args.steps
     total_stage_ms = sum(v[0] for v in stages.values()) / args.steps
@@ -513,10 +541,15 @@ def run_ours(args):
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     peak_lmul = 152 * 32 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / SHFL_PER_LIMB_MUL
     ach_lmul = work / (fft_ms / 1e3)
-    roof = {"bound": "alu", "kernel": "k_fft_pass (all FFT_LCH / iFFT_LCH passes; the "
-                                      "stage times include the changeRepr kernel ahead of them)",
+    traffic = fft_traffic_per_launch()
+    roof = {"bound": "alu", "kernel": "k_fft_pass (all FFT_LCH / iFFT_LCH passes)",
             "achieved": ach_lmul / 1e9, "peak": peak_lmul / 1e9,
-            "unit": "G limb-mult/s", "frac": ach_lmul / peak_lmul, "traffic": None,
+            "unit": "G limb-mult/s", "frac": ach_lmul / peak_lmul,
+            "traffic": traffic["bytes"] if traffic else None,
+            "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+            "traffic_source": traffic["source"] if traffic else
+            "none for these kernel sources (captured for other sources, or no capture)",
+            "algorithmic_bytes_per_launch": None,
             "work_per_launch": work / max(1, fft_launches),
             "avg_launch_ms": fft_ms / max(1, fft_launches),
             "share_of_step": fft_ms / max(1e-9, total_stage_ms),
@@ -524,6 +557,7 @@ def run_ours(args):
                            "per F~_{2^32} limb product"}
     plan_depth = max(1, min(7, int(tuned.get("fft_depth", 7))))
     fbytes = fft_hbm_bytes(N, M, la, lb, plan_depth)
+    roof["algorithmic_bytes_per_launch"] = fbytes / max(1, fft_launches)
     roof_hbm = {"bound": "hbm", "kernel": "k_fft_pass", "achieved": fbytes / (fft_ms / 1e3) / 1e9,
                 "peak": hbm, "unit": "GB/s", "frac": fbytes / (fft_ms / 1e3) / 1e9 / hbm,
                 "bytes_per_product": fbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}

@@ -260,17 +260,19 @@ GF2X_API int gf2x_stage_ichrepr_combine(const uint64_t *F, uint64_t n, uint64_t 
 /* ---- Per-stage timing (the component profile of the paper's Table 4) ----*/
 
 /* on = 1: every later product records a CUDA event before and after each of
- * its stage groups on the stream it runs on: split, basis_cvt, chrepr_fft_a
- * (changeRepr + FFT_LCH of a), chrepr_fft_b (changeRepr + top FFT_LCH layers
- * of b), fft_pointmul_ifft_bottom (bottom FFT layers of b + pointmul + bottom
- * iFFT layers), ifft_top, ibasis_cvt, ichrepr_combine.  on = 0 stops. */
+ * its stage groups on the stream it runs on: split, basis_cvt, chrepr
+ * (changeRepr of the blocks of a transform with strided passes; a transform
+ * without them converts in its bottom pass), fft_a (FFT_LCH of a), fft_b (top
+ * FFT_LCH layers of b), fft_pointmul_ifft_bottom (bottom FFT layers of b +
+ * pointmul + bottom iFFT layers), ifft_top, ibasis_cvt, ichrepr_combine.
+ * on = 0 stops. */
 GF2X_API int gf2x_profile_enable(int on);
 
 /* Drops recorded events and zeroes the sums. */
 GF2X_API int gf2x_profile_reset(void);
 
 /* Waits for the recorded events, then returns for stage index `stage`
- * (0 .. 7, order above) the summed elapsed milliseconds, the number of
+ * (0 .. 8, order above) the summed elapsed milliseconds, the number of
  * kernel launches in those stages and the number of stage executions. */
 GF2X_API int gf2x_profile_read(int stage, double *ms, uint64_t *launches,
                                uint64_t *calls);

@@ -182,9 +182,9 @@ bool overlap(const void *a, size_t na, const void *b, size_t nb) {
 // When enabled, plan_run records a CUDA event before and after each stage on
 // the stream it runs on; gf2x_profile_read waits for the events and sums the
 // elapsed times per stage.
-const char *kStageNames[ST_COUNT] = {"split",        "basis_cvt",      "chrepr_fft_a",
-                                     "chrepr_fft_b", "fft_pointmul_ifft_bottom", "ifft_top",
-                                     "ibasis_cvt",   "ichrepr_combine"};
+const char *kStageNames[ST_COUNT] = {"split",      "basis_cvt", "chrepr",
+                                     "fft_a",      "fft_b",     "fft_pointmul_ifft_bottom",
+                                     "ifft_top",   "ibasis_cvt", "ichrepr_combine"};
 
 struct ProfRec {
     int stage;

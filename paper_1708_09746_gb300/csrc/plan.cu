@@ -146,23 +146,26 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
     auto end = [&](uint64_t n) {
         if (hook) hook->end(n);
     };
-    // Split, BasisCvt, changeRepr + FFT_LCH of a (changeRepr fused into the
-    // first pass; the layers above log2 Pa are fan-outs: the pass reads the
-    // blocks periodically)
+    // Split, BasisCvt, changeRepr + FFT_LCH of a (the layers above log2 Pa
+    // are fan-outs: the first pass reads the P converted blocks periodically)
     begin(ST_SPLIT);
     launch_split_pad(one_a, many_a, count, WA, p->Pa, sW, s);
     end(1);
     begin(ST_BCVT);
     end(run_basis_cvt<uint64_t>(WA, p->pa_log, p->lv_a, 0, s, count, sW, p->tune.bcvt));
-    begin(ST_FFT_A);
     // with strided passes: changeRepr into ST, which the first pass reads
     // periodically; a lone bottom pass reads the blocks and converts them itself
     const bool st_a = p->fft_a.n > 1;
-    if (st_a) launch_chrepr_stage(WA, p->Pa, sW, ST, sF, count, T, s);
+    if (st_a) {
+        begin(ST_CHREPR);
+        launch_chrepr_stage(WA, p->Pa, sW, ST, sF, count, T, s);
+        end(1);
+    }
+    begin(ST_FFT_A);
     for (int i = 0; i < p->fft_a.n; i++)
         launch_fft_pass(p->fft_a.v[i], p->M, FA, (i == 0 && !st_a) ? WA : nullptr, p->Pa, nullptr, T,
                         st, s, count, sF, sW, (i == 0 && st_a) ? ST : nullptr);
-    end(p->fft_a.n + (st_a ? 1 : 0));
+    end(p->fft_a.n);
     // the same for b, then its top FFT layers
     if (b_ready) cudaStreamWaitEvent(s, b_ready, 0);
     begin(ST_SPLIT);
@@ -170,12 +173,16 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
     end(1);
     begin(ST_BCVT);
     end(run_basis_cvt<uint64_t>(WB, p->pb_log, p->lv_b, 0, s, count, sW, p->tune.bcvt));
+    if (p->fft_b.n > 0) {
+        begin(ST_CHREPR);
+        launch_chrepr_stage(WB, p->Pb, sW, ST, sF, count, T, s);
+        end(1);
+    }
     begin(ST_FFT_B);
-    if (p->fft_b.n > 0) launch_chrepr_stage(WB, p->Pb, sW, ST, sF, count, T, s);
     for (int i = 0; i < p->fft_b.n; i++)
         launch_fft_pass(p->fft_b.v[i], p->M, FB, nullptr, p->Pb, nullptr, T, st, s, count, sF, sW,
                         i == 0 ? ST : nullptr);
-    end(p->fft_b.n + (p->fft_b.n > 0));
+    end(p->fft_b.n);
     // bottom layers of FFT(b), pointmul, bottom layers of iFFT_LCH
     begin(ST_FUSED);
     launch_fft_pass(p->fused, p->M, FB, p->fft_b.n == 0 ? WB : nullptr, p->Pb, FA, T, st, s, count,

@@ -48,7 +48,9 @@ namespace gf2x {
 constexpr int kMaxLogN = 28;  // FFT points N <= 2^28
 
 // Stage groups timed by the profiling hook (order of gf2x_profile_read).
-enum Stage { ST_SPLIT, ST_BCVT, ST_FFT_A, ST_FFT_B, ST_FUSED, ST_IFFT, ST_IBCVT, ST_OUT, ST_COUNT };
+enum Stage {
+    ST_SPLIT, ST_BCVT, ST_CHREPR, ST_FFT_A, ST_FFT_B, ST_FUSED, ST_IFFT, ST_IBCVT, ST_OUT, ST_COUNT
+};
 
 struct StageHook {
     virtual void begin(int stage) = 0;
