@@ -304,13 +304,16 @@ def measure_sizes(G, torch, W, dev, stream, flush):
     products) for the larger single-product workloads."""
     import numpy as np
     res = {}
-    for name in ("c1_2^29", "c2_2^30", "c2_2^32"):
+    for name in ("c1_2^29", "c1_2^28x2^16", "c2_2^30", "c2_2^32"):
         a, na, b, nb = W.make_workload(name)
         da = torch.from_numpy(a.view(np.int64)).to(dev)
         db = torch.from_numpy(b.view(np.int64)).to(dev)
         del a, b
         out = torch.empty(G.gf2x_out_words(na, nb), dtype=torch.int64, device=dev)
-        tuned = G.gf2x_autotune(na, nb, 2)
+        # unbalanced operands run by chunks of the long one (their own plan,
+        # default parameters); the others with the shape's autotuned plan
+        chunked = max(na, nb) >= 4 * 64 * max(512, 1 << max(0, (min(na, nb) + 63) // 64 - 1).bit_length())
+        tuned = "chunked product, default plan parameters" if chunked else G.gf2x_autotune(na, nb, 2)
         evs = []
         with torch.cuda.stream(stream):
             for i in range(4):

@@ -356,8 +356,31 @@ int check_operands(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint6
     return GF2X_OK;
 }
 
+// Unbalanced operands: the product by chunks of the long operand against one
+// transform of the short one (plan_run_chunked).
+int mul_chunked(const uint64_t *x, uint64_t x_bits, const uint64_t *y, uint64_t y_bits,
+                uint64_t *out, const ChunkShape &cs, cudaStream_t s) {
+    std::shared_ptr<gf2x_plan> pc;
+    int rc = cached_plan(y_bits, 64 * cs.L, &pc);
+    if (rc) return rc;
+    const DevTables *T;
+    if ((rc = get_tables(&T))) return rc;
+    void *ws = nullptr;
+    if ((rc = ws_alloc(&ws, chunked_ws_bytes(pc.get(), cs.C), s))) return rc;
+    StageTimer tm(s);
+    rc = plan_run_chunked(pc.get(), cs, x, x_bits, y, y_bits, out, ws, s, T, device_status(), &tm);
+    ws_free(ws, s);
+    if (rc) return GF2X_ECUDA;
+    return check_launch();
+}
+
 int mul_on_stream(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64_t nb_bits,
                   uint64_t *out, cudaStream_t s) {
+    ChunkShape cs;
+    if (chunk_shape(words_of(na_bits), words_of(nb_bits), &cs))
+        return mul_chunked(a, na_bits, b, nb_bits, out, cs, s);
+    if (chunk_shape(words_of(nb_bits), words_of(na_bits), &cs))
+        return mul_chunked(b, nb_bits, a, na_bits, out, cs, s);
     std::shared_ptr<gf2x_plan> p;
     int rc = cached_plan(na_bits, nb_bits, &p);
     if (rc) return rc;

@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         if (a.mode == 2) {  // pointmul with the other operand's transform
             for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) {
                 const uint64_t idx = base | ((uint64_t)(q >> c) << a.k_lo) | (q & cmask);
-                s[q] = mt_gmul128(M, s[q], __ldg(a.FA + y * a.strideF + idx));
+                s[q] = mt_gmul128(M, s[q], __ldg(a.FA + y * a.strideFA + idx));
             }
             __syncthreads();
         }
@@ -722,7 +722,7 @@ static int resident_ctas(int threads, size_t smem) {
 
 int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,
                     const uint4 *FA, const DevTables *T, int *status, cudaStream_t s, int count,
-                    uint64_t strideF, uint64_t strideW, const uint4 *Fsrc) {
+                    uint64_t strideF, uint64_t strideW, const uint4 *Fsrc, uint64_t strideFA) {
     ensure_smem_attr(reinterpret_cast<const void *>(k_fft_pass), 227 * 1024);
     FftPassArgs a;
     a.F = F;
@@ -745,6 +745,7 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
     a.status = status;
     a.count = count;
     a.strideF = strideF;
+    a.strideFA = strideFA == ~0ull ? strideF : strideFA;
     a.strideW = strideW;
     a.nbuf = p.nbuf;
     const uint64_t tiles = ((1ull << M) >> (p.g + p.c)) * (uint64_t)count;

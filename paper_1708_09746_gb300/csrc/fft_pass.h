@@ -41,7 +41,8 @@ struct FftPassArgs {
     int M;        // log2 of the transform length
     int *status;  // device status word (a bounded wait that ran out stores GF2X_ETIMEOUT)
     int count;    // products in the launch: product y at F + y * strideF,
-    uint64_t strideF, strideW;  // g64 + y * strideW, FA + y * strideF
+    uint64_t strideF, strideW;  // g64 + y * strideW, FA + y * strideFA
+    uint64_t strideFA;          // 0: one transform FA shared by all products
     int nbuf;     // tile buffers (1 or 2)
 };
 
@@ -93,7 +94,7 @@ constexpr int kFftGlobalMax = 7;  // keeps c = 12 - g >= 5 (warp-uniform multipl
 int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,
                     const uint4 *FA, const DevTables *T, int *status, cudaStream_t s,
                     int count = 1, uint64_t strideF = 0, uint64_t strideW = 0,
-                    const uint4 *Fsrc = nullptr);
+                    const uint4 *Fsrc = nullptr, uint64_t strideFA = ~0ull);
 
 void launch_pointmul_mt(const uint4 *A, const uint4 *B, uint4 *C, uint64_t n, const DevTables *T,
                         cudaStream_t s);

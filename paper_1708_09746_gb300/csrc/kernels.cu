@@ -596,7 +596,8 @@ __global__ void __launch_bounds__(256) k_ichrepr_combine(const uint4 *__restrict
                                                          uint64_t stride, OutputDesc one,
                                                          const OutputDesc *__restrict__ many,
                                                          const DevTables *__restrict__ T,
-                                                         uint64_t j_begin, uint64_t j_end) {
+                                                         uint64_t j_begin, uint64_t j_end,
+                                                         int accumulate) {
     __shared__ __align__(16) uint32_t tab[4 * 4 * 7 * 32];
     const uint4 *src = reinterpret_cast<const uint4 *>(&T->psi_shfl[0][0][0][0]);
     for (int i = threadIdx.x; i < 4 * 4 * 7 * 32 / 4; i += blockDim.x)
@@ -664,6 +665,7 @@ __global__ void __launch_bounds__(256) k_ichrepr_combine(const uint4 *__restrict
                 uint64_t v = ((uint64_t)r[k][0] | ((uint64_t)r[k][1] << 32)) ^
                              ((uint64_t)hz | ((uint64_t)hw << 32));
                 if (j == d.words - 1) v &= d.mask;
+                if (accumulate) v ^= d.out[j];
                 d.out[j] = v;
             }
         }
@@ -1012,14 +1014,35 @@ void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const De
 void launch_ichrepr_combine(const uint4 *F, uint64_t n, uint64_t stride, const OutputDesc &one,
                             const OutputDesc *many, int count, uint64_t max_words,
                             const DevTables *T, cudaStream_t s, uint64_t j_begin,
-                            uint64_t j_end) {
+                            uint64_t j_end, bool accumulate) {
     // a few resident CTAs per SM, each loading the 14 KiB of tables once; a
     // warp takes chunks of 32 kCombineK - 1 output words
     const uint64_t per = std::max<uint64_t>(1, (uint64_t)num_sms() * 4 / (uint64_t)std::max(count, 1));
     const uint64_t span = std::min(j_end, max_words) > j_begin ? std::min(j_end, max_words) - j_begin : 0;
     const uint64_t need = (span + 8 * (32 * kCombineK - 1) - 1) / (8 * (32 * kCombineK - 1));
     dim3 grid((unsigned)std::max<uint64_t>(1, std::min(need, per)), count);
-    k_ichrepr_combine<<<grid, 256, 0, s>>>(F, n, stride, one, many, T, j_begin, j_end);
+    k_ichrepr_combine<<<grid, 256, 0, s>>>(F, n, stride, one, many, T, j_begin, j_end,
+                                           accumulate ? 1 : 0);
+}
+
+__global__ void k_chunk_descs(const uint64_t *x, uint64_t xw, uint64_t x_mask, uint64_t L,
+                              uint64_t C, uint64_t *out, uint64_t out_words, uint64_t out_mask,
+                              uint64_t chunk_words, OperandDesc *dx, OutputDesc *dout) {
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= C) return;
+    const uint64_t nw = xw - i * L < L ? xw - i * L : L;
+    dx[i] = OperandDesc{x + i * L, nw, i == C - 1 ? x_mask : ~0ull};
+    const uint64_t left = out_words - i * L;
+    const uint64_t w = chunk_words < left ? chunk_words : left;
+    const uint64_t slot = (i & 1) ? (C + 1) / 2 + i / 2 : i / 2;
+    dout[slot] = OutputDesc{out + i * L, w, i * L + w == out_words ? out_mask : ~0ull};
+}
+
+void launch_chunk_descs(const uint64_t *x, uint64_t xw, uint64_t x_mask, uint64_t L, uint64_t C,
+                        uint64_t *out, uint64_t out_words, uint64_t out_mask,
+                        uint64_t chunk_words, OperandDesc *dx, OutputDesc *dout, cudaStream_t s) {
+    k_chunk_descs<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(x, xw, x_mask, L, C, out, out_words,
+                                                             out_mask, chunk_words, dx, dout);
 }
 
 }  // namespace gf2x

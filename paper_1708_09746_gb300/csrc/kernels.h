@@ -82,10 +82,21 @@ void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const De
 
 // changeRepr^-1 + InterleavedCombine of `count` products: product y reads n
 // elements at F + y * stride and writes many[y] (or `one`); max_words bounds
-// the output lengths.  Only output words [j_begin, j_end) are written.
+// the output lengths.  Only output words [j_begin, j_end) are written; with
+// `accumulate` they are XORed into the output instead of stored.
 void launch_ichrepr_combine(const uint4 *F, uint64_t n, uint64_t stride, const OutputDesc &one,
                             const OutputDesc *many, int count, uint64_t max_words,
                             const DevTables *T, cudaStream_t s, uint64_t j_begin = 0,
-                            uint64_t j_end = ~0ull);
+                            uint64_t j_end = ~0ull, bool accumulate = false);
+
+// Descriptors of the chunked (unbalanced) product: chunk i of the long operand
+// x (xw words, last word masked by x_mask) is x + i * L, min(L, xw - i * L)
+// words; its product with the short operand (yw words) lands at out + i * L,
+// min(chunk_words, out_words - i * L) words (the last one masked by out_mask).
+// dx[i] for every chunk; dout holds the even chunks' outputs, then the odd
+// ones'.
+void launch_chunk_descs(const uint64_t *x, uint64_t xw, uint64_t x_mask, uint64_t L, uint64_t C,
+                        uint64_t *out, uint64_t out_words, uint64_t out_mask,
+                        uint64_t chunk_words, OperandDesc *dx, OutputDesc *dout, cudaStream_t s);
 
 }  // namespace gf2x

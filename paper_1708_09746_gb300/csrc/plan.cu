@@ -221,6 +221,111 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
 
 uint64_t mask_of_bits(uint64_t bits) { return (bits % 64) ? ((1ull << (bits % 64)) - 1) : ~0ull; }
 
+bool chunk_shape(uint64_t xw, uint64_t yw, ChunkShape *cs) {
+    if (yw == 0 || xw < yw) return false;
+    // at most 2^15 chunks (one launch row per chunk)
+    const uint64_t L = 1ull << std::max(log2_ceil(std::max<uint64_t>(yw, 512)),
+                                        log2_ceil((xw + 32767) / 32768));
+    const uint64_t C = (xw + L - 1) / L;
+    if (C < 4) return false;
+    cs->L = L;
+    cs->C = C;
+    return true;
+}
+
+// C chunk workspaces of the chunk plan (chunk i's FB, WB, ST at + i * ws_bytes;
+// block 0's FA, WA also hold y's transform), then the descriptors.
+size_t chunked_ws_bytes(const gf2x_plan *pc, uint64_t C) {
+    const size_t descs = C * (sizeof(OperandDesc) + sizeof(OutputDesc));
+    return C * pc->ws_bytes + ((descs + 255) & ~size_t(255));
+}
+
+int plan_run_chunked(const gf2x_plan *pc, const ChunkShape &cs, const uint64_t *x,
+                     uint64_t x_bits, const uint64_t *y, uint64_t y_bits, uint64_t *out, void *ws,
+                     cudaStream_t s, const DevTables *T, int *st, StageHook *hook) {
+    const uint64_t C = cs.C, L = cs.L, xw = words_of(x_bits);
+    if (C > (uint64_t)INT32_MAX / 2) return -1;
+    const int count = (int)C;
+    char *base = static_cast<char *>(ws);
+    const size_t blk = pc->ws_bytes;
+    uint4 *FA = reinterpret_cast<uint4 *>(base + pc->off_fa);
+    uint4 *FB = reinterpret_cast<uint4 *>(base + pc->off_fb);
+    uint64_t *WA = reinterpret_cast<uint64_t *>(base + pc->off_wa);
+    uint64_t *WB = reinterpret_cast<uint64_t *>(base + pc->off_wb);
+    uint4 *ST = reinterpret_cast<uint4 *>(base + pc->off_st);
+    OperandDesc *dx = reinterpret_cast<OperandDesc *>(base + C * blk);
+    OutputDesc *dout = reinterpret_cast<OutputDesc *>(dx + C);
+    const uint64_t sF = blk / 16, sW = blk / 8;
+    const uint64_t out_words = words_of(x_bits + y_bits - 1);
+    auto begin = [&](int stage) {
+        if (hook) hook->begin(stage);
+    };
+    auto end = [&](uint64_t n) {
+        if (hook) hook->end(n);
+    };
+    // y: Split, BasisCvt, changeRepr and every forward layer, once
+    const OperandDesc one_y{y, words_of(y_bits), mask_of_bits(y_bits)};
+    begin(ST_SPLIT);
+    launch_split_pad(one_y, nullptr, 1, WA, pc->Pa, sW, s);
+    launch_chunk_descs(x, xw, mask_of_bits(x_bits), L, C, out, out_words,
+                       mask_of_bits(x_bits + y_bits - 1), pc->out_words, dx, dout, s);
+    end(2);
+    begin(ST_BCVT);
+    end(run_basis_cvt<uint64_t>(WA, pc->pa_log, pc->lv_a, 0, s, 1, sW, pc->tune.bcvt));
+    const bool st_a = pc->fft_a.n > 1;
+    if (st_a) {
+        begin(ST_CHREPR);
+        launch_chrepr_stage(WA, pc->Pa, sW, ST, sF, 1, T, s);
+        end(1);
+    }
+    begin(ST_FFT_A);
+    for (int i = 0; i < pc->fft_a.n; i++)
+        launch_fft_pass(pc->fft_a.v[i], pc->M, FA, (i == 0 && !st_a) ? WA : nullptr, pc->Pa,
+                        nullptr, T, st, s, 1, sF, sW, (i == 0 && st_a) ? ST : nullptr);
+    end(pc->fft_a.n);
+    // the chunks, as operand b of C products sharing y's transform
+    const OperandDesc none{nullptr, 0, 0};
+    begin(ST_SPLIT);
+    launch_split_pad(none, dx, count, WB, pc->Pb, sW, s);
+    end(1);
+    begin(ST_BCVT);
+    end(run_basis_cvt<uint64_t>(WB, pc->pb_log, pc->lv_b, 0, s, count, sW, pc->tune.bcvt));
+    if (pc->fft_b.n > 0) {
+        begin(ST_CHREPR);
+        launch_chrepr_stage(WB, pc->Pb, sW, ST, sF, count, T, s);
+        end(1);
+    }
+    begin(ST_FFT_B);
+    for (int i = 0; i < pc->fft_b.n; i++)
+        launch_fft_pass(pc->fft_b.v[i], pc->M, FB, nullptr, pc->Pb, nullptr, T, st, s, count, sF,
+                        sW, i == 0 ? ST : nullptr);
+    end(pc->fft_b.n);
+    begin(ST_FUSED);
+    launch_fft_pass(pc->fused, pc->M, FB, pc->fft_b.n == 0 ? WB : nullptr, pc->Pb, FA, T, st, s,
+                    count, sF, sW, nullptr, 0);
+    end(1);
+    begin(ST_IFFT);
+    for (int i = 0; i < pc->ifft_top.n; i++)
+        launch_fft_pass(pc->ifft_top.v[i], pc->M, FB, nullptr, 0, nullptr, T, st, s, count, sF, sW);
+    end(pc->ifft_top.n);
+    begin(ST_IBCVT);
+    end(run_basis_cvt<uint4>(FB, pc->M, pc->lv_c, 1, s, count, sF, pc->tune.bcvt));
+    // the chunk products overlap their neighbours (y's words - 1 at most, no
+    // more than L): the even chunks, then the odd ones, XORed into a zeroed
+    // output
+    begin(ST_OUT);
+    cudaMemsetAsync(out, 0, 8 * out_words, s);
+    const OutputDesc none_out{nullptr, 0, 0};
+    const int even = (count + 1) / 2, odd = count / 2;
+    launch_ichrepr_combine(FB, pc->N, 2 * sF, none_out, dout, even, pc->out_words, T, s, 0, ~0ull,
+                           true);
+    if (odd > 0)
+        launch_ichrepr_combine(FB + sF, pc->N, 2 * sF, none_out, dout + even, odd, pc->out_words, T,
+                               s, 0, ~0ull, true);
+    end(odd > 0 ? 2 : 1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
 int plan_run_core(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out,
                   void *ws, cudaStream_t s, const DevTables *T, int *st, StageHook *hook,
                   cudaEvent_t b_ready, const OutputDrain *drain) {

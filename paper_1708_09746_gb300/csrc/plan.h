@@ -105,6 +105,23 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
 
 uint64_t mask_of_bits(uint64_t bits);
 
+// The unbalanced product by chunks.  When the long operand x has at least
+// four times as many words as the short operand y, x is cut into C chunks of
+// L words (L a power of two >= the words of y, at least 512), each chunk is
+// multiplied by y with a transform of about 2L points instead of one of about
+// xw points, and the chunk products are XORed into the output at i * L.  y is
+// converted and transformed once (all layers); every chunk's bottom pass
+// multiplies by that one transform.  The chunk plan pc is the plan of y (as
+// operand a) times a chunk of 64 L bits (as operand b).
+struct ChunkShape {
+    uint64_t L = 0, C = 0;
+};
+bool chunk_shape(uint64_t xw, uint64_t yw, ChunkShape *cs);
+size_t chunked_ws_bytes(const gf2x_plan *pc, uint64_t C);
+int plan_run_chunked(const gf2x_plan *pc, const ChunkShape &cs, const uint64_t *x,
+                     uint64_t x_bits, const uint64_t *y, uint64_t y_bits, uint64_t *out, void *ws,
+                     cudaStream_t s, const DevTables *T, int *status, StageHook *hook);
+
 // Host image of the size-independent device tables.
 void fill_dev_tables(DevTables *h);
 

@@ -44,6 +44,34 @@ def test_small_and_ragged(na, nb):
     assert np.array_equal(got, P.mul(a, na, b, nb))
 
 
+# Unbalanced operands (the long one at least four chunks of the short one's
+# power-of-two size, 512 words or more) take the chunked product: chunks of
+# the long operand times one transform of the short one, XORed into the
+# output at their offsets; the last chunk may be one word
+UNBALANCED = [(64 * 2048, 64 * 100), (64 * 100 + 5, 64 * 2048 + 1), (64 * 5000 + 3, 1),
+              (64 * 4096 * 4 + 17, 64 * 600 + 3), (64 * 2049, 64 * 512), (64 * 2048, 64 * 513),
+              (64 * 512 * 7 + 1, 64 * 512 - 7)]
+
+
+@pytest.mark.parametrize("na,nb", UNBALANCED)
+def test_unbalanced_chunked(na, nb):
+    a, b = W.operand_pair(na * 3 + nb, na, nb)
+    got = gpu_mul(a, na, b, nb)
+    assert np.array_equal(got, P.mul(a, na, b, nb))
+
+
+def test_unbalanced_chunked_async_stream():
+    na, nb = 64 * 3000 + 9, 64 * 200 + 1
+    a, b = W.operand_pair(4242, na, nb)
+    want = P.mul(a, na, b, nb)
+    da, db = to_dev(a), to_dev(b)
+    out = empty_dev(len(want))
+    s = torch.cuda.Stream()
+    G.gf2x_mul_async(da, na, db, nb, out, s)
+    s.synchronize()
+    assert np.array_equal(from_dev(out, len(want)), want)
+
+
 def test_random_sizes_sweep():
     rng = np.random.default_rng(77)
     for it in range(40):
