@@ -525,7 +525,7 @@ __global__ void k_chrepr(const uint64_t *__restrict__ g, uint64_t pmask, uint4 *
 // consecutive blocks (8 per lane), one output word of phi at a time.
 constexpr int kChreprK = 8;
 
-__global__ void __launch_bounds__(256) k_chrepr_stage(const uint64_t *__restrict__ g, uint64_t P,
+__global__ void __launch_bounds__(256, 2) k_chrepr_stage(const uint64_t *__restrict__ g, uint64_t P,
                                                       uint64_t strideW, uint4 *__restrict__ F,
                                                       uint64_t strideF,
                                                       const DevTables *__restrict__ T) {
@@ -592,7 +592,7 @@ __global__ void __launch_bounds__(256) k_chrepr_stage(const uint64_t *__restrict
 // element.
 constexpr int kCombineK = 8;
 
-__global__ void __launch_bounds__(256) k_ichrepr_combine(const uint4 *__restrict__ F, uint64_t n,
+__global__ void __launch_bounds__(256, 2) k_ichrepr_combine(const uint4 *__restrict__ F, uint64_t n,
                                                          uint64_t stride, OutputDesc one,
                                                          const OutputDesc *__restrict__ many,
                                                          const DevTables *__restrict__ T,
