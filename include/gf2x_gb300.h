@@ -76,7 +76,14 @@ GF2X_API uint64_t gf2x_fft_points(uint64_t na_bits, uint64_t nb_bits);
 /* ---- One-shot products ---------------------------------------------------*/
 
 /* c = a * b (Alg. 5).  Synchronous: enqueues on the legacy default stream,
- * allocates its workspace there (stream-ordered) and waits for completion. */
+ * allocates its workspace there (stream-ordered) and waits for completion.
+ * Unbalanced operands (the longer at least four chunks of L words, L the
+ * shorter's word count rounded up to a power of two, at least 512) are
+ * multiplied by chunks: every chunk of the longer operand times one transform
+ * of the shorter (transforms of about 2L points), the chunk products XORed
+ * into the output at their offsets (distributivity; the same c).  gf2x_mul
+ * and gf2x_mul_async do this; plans, batches, the server and the host-buffer
+ * call use one transform of the whole product. */
 GF2X_API int gf2x_mul(const uint64_t *a, uint64_t na_bits, const uint64_t *b,
              uint64_t nb_bits, uint64_t *out);
 
