@@ -30,6 +30,7 @@ import os
 import re
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -101,7 +102,10 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        # raw samples go to a scratch file (GF2X_CLOCKS_DIR, else the system's
+        # temporary directory); the JSON line carries their summary
+        self.path = os.path.join(os.environ.get("GF2X_CLOCKS_DIR", tempfile.gettempdir()),
+                                 "gf2x_clocks_bench_%d.csv" % os.getpid())
 
     def start(self):
         try:

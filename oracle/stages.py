@@ -10,7 +10,7 @@ coefficient of the tower basis vector v_i (Def. 3.1), so the integer i is the
 representative \\bar{i} (Def. 3.2) and the subfield \\tilde F_{2^(2^k)} is
 the low 2^k bits.
 
-Readings of the paper used here (each also listed in the design doc):
+Readings of the paper used here:
   * changeRepr (Alg. 5, Sec. 4.3): a 64-bit block p(z) is sent to p(r) with
     r = x_7 = v_64, whose minimal polynomial has degree 128, so the map is a
     ring homomorphism on products of degree <= 126 (Sec. 2.1 allows any
