@@ -546,7 +546,15 @@ def run_ours(args):
     total_stage_ms = sum(v[0] for v in stages.values()) / args.steps
     work, _, M, la, lb = fft_work(na, nb)
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak_lmul = 152 * 32 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / SHFL_PER_LIMB_MUL
+    # the shuffle issue rate measured on this device (gf2x_probe_pipes); the
+    # nominal one shuffle per SM per clock if the probe fails
+    try:
+        probe = G.gf2x_probe_pipes()
+    except Exception as e:  # report the failure, keep the nominal peak
+        probe = {"error": str(e)}
+    shfl_rate = probe.get("shfl_per_clk_sm") or 1.0
+    sms = probe.get("sms") or 152
+    peak_lmul = sms * shfl_rate * 32 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / SHFL_PER_LIMB_MUL
     ach_lmul = work / (fft_ms / 1e3)
     traffic = fft_traffic_per_launch()
     roof = {"bound": "alu", "kernel": "k_fft_pass (all FFT_LCH / iFFT_LCH passes)",
@@ -560,8 +568,13 @@ def run_ours(args):
             "work_per_launch": work / max(1, fft_launches),
             "avg_launch_ms": fft_ms / max(1, fft_launches),
             "share_of_step": fft_ms / max(1e-9, total_stage_ms),
-            "peak_source": "derived: 152 SMs x 32 lanes x max SM clock / 7 warp shuffles "
-                           "per F~_{2^32} limb product"}
+            "peak_source": ("measured shuffle issue rate (gf2x_probe_pipes: %.3f warp shuffles "
+                            "per SM clock) x %d SMs x 32 lanes x max SM clock / 7 shuffles per "
+                            "F~_{2^32} limb product" % (shfl_rate, sms))
+            if "shfl_per_clk_sm" in probe else
+            "derived: 152 SMs x 32 lanes x max SM clock / 7 warp shuffles per F~_{2^32} "
+            "limb product (probe failed: %s)" % probe.get("error"),
+            "pipe_probe": probe}
     plan_depth = max(1, min(7, int(tuned.get("fft_depth", 7))))
     fbytes = fft_hbm_bytes(N, M, la, lb, plan_depth)
     roof["algorithmic_bytes_per_launch"] = fbytes / max(1, fft_launches)

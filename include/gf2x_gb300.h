@@ -287,6 +287,18 @@ GF2X_API int gf2x_profile_read(int stage, double *ms, uint64_t *launches,
 /* Name of stage index `stage`, or "" if out of range. */
 GF2X_API const char *gf2x_profile_stage_name(int stage);
 
+/* ---- Pipe throughput probe ------------------------------------------------*/
+
+/* Measures, on the current device, the issue rate of the three instruction
+ * kinds the product path is bound by, in warp instructions per SM clock:
+ * shfl.sync.idx (the shuffle tables of the butterfly multiply), three-input
+ * XOR (lop3) and conflict-free 32-bit shared-memory loads.  One CTA of 32 warps
+ * per SM runs eight independent chains of each kind; cycles come from the SM
+ * clock.  *sm_count receives the SM count.  Takes a few milliseconds; returns a
+ * status. */
+GF2X_API int gf2x_probe_pipes(double *shfl_per_clk_sm, double *xor_per_clk_sm,
+                              double *lds_per_clk_sm, int *sm_count);
+
 /* ---- Allocation-free product --------------------------------------------*/
 
 /* Scratch the allocation-free product keeps in a static device array on every

@@ -23,7 +23,7 @@ __all__ = [
     "gf2x_profile_reset", "gf2x_profile_read", "gf2x_profile_stage_name", "gf2x_mul_noalloc",
     "gf2x_batch_create", "gf2x_batch_workspace_bytes", "gf2x_batch_execute", "gf2x_batch_destroy",
     "gf2x_server_create", "gf2x_server_submit", "gf2x_server_wait", "gf2x_server_stats",
-    "gf2x_server_reset_stats", "gf2x_server_destroy", "LIB_PATH",
+    "gf2x_server_reset_stats", "gf2x_server_destroy", "gf2x_probe_pipes", "LIB_PATH",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -79,6 +79,8 @@ _SIGS = {
     "gf2x_profile_read": (_int, [_int, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "gf2x_profile_stage_name": (ctypes.c_char_p, [_int]),
+    "gf2x_probe_pipes": (_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "gf2x_mul_noalloc": (_int, [_vp, _u64, _vp, _u64, _vp, _vp]),
     "gf2x_batch_create": (_int, [_int, _vp, _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]),
     "gf2x_batch_workspace_bytes": (_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
@@ -289,6 +291,17 @@ def gf2x_profile_read(stage):
 
 def gf2x_profile_stage_name(stage):
     return load().gf2x_profile_stage_name(int(stage)).decode()
+
+
+def gf2x_probe_pipes():
+    """Issue rates (warp instructions per SM clock) of shfl.sync.idx, lop3 and
+    conflict-free shared-memory loads on the current device, and its SM count."""
+    sh, xo, ld = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    n = ctypes.c_int()
+    _check(load().gf2x_probe_pipes(ctypes.byref(sh), ctypes.byref(xo), ctypes.byref(ld),
+                                   ctypes.byref(n)), "gf2x_probe_pipes")
+    return {"shfl_per_clk_sm": sh.value, "xor_per_clk_sm": xo.value,
+            "lds_per_clk_sm": ld.value, "sms": n.value}
 
 
 def profile_all():
