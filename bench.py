@@ -316,8 +316,10 @@ def measure_sizes(G, torch, W, dev, stream, flush):
         out = torch.empty(G.gf2x_out_words(na, nb), dtype=torch.int64, device=dev)
         # unbalanced operands run by chunks of the long one (their own plan,
         # default parameters); the others with the shape's autotuned plan
-        chunked = max(na, nb) >= 4 * 64 * max(512, 1 << max(0, (min(na, nb) + 63) // 64 - 1).bit_length())
-        tuned = "chunked product, default plan parameters" if chunked else G.gf2x_autotune(na, nb, 2)
+        chunking = G.gf2x_chunking(na, nb)
+        tuned = ("chunked product (%d chunks of %d words, %d-point transforms), default plan "
+                 "parameters" % (chunking[1], chunking[0], chunking[2])
+                 if chunking[1] else G.gf2x_autotune(na, nb, 2))
         evs = []
         with torch.cuda.stream(stream):
             for i in range(4):

@@ -68,10 +68,19 @@ GF2X_API const char *gf2x_strerror(int status);
  * ceil((na+nb-1)/64), or 0 if either size is 0. */
 GF2X_API uint64_t gf2x_out_words(uint64_t na_bits, uint64_t nb_bits);
 
-/* Number of FFT points N the library uses for these operand sizes: the
- * smallest power of two >= na_w + nb_w - 1 (at least 2), na_w = ceil(na/64).
- * 0 if either size is 0. */
+/* Number of FFT points N of the product as one transform: the smallest power
+ * of two >= na_w + nb_w - 1 (at least 2), na_w = ceil(na/64); 0 if either
+ * size is 0.  Plans, batches and the server use it; the one-shot calls use it
+ * unless gf2x_chunking reports chunks. */
 GF2X_API uint64_t gf2x_fft_points(uint64_t na_bits, uint64_t nb_bits);
+
+/* How gf2x_mul / gf2x_mul_async split unbalanced operands (see below): the
+ * chunk length of the longer operand in words, the number of chunks and the
+ * transform length of one chunk product; all three 0 when the product runs as
+ * one transform of gf2x_fft_points points.  Host-only (no GPU needed);
+ * GF2X_EINVAL for a null pointer. */
+GF2X_API int gf2x_chunking(uint64_t na_bits, uint64_t nb_bits, uint64_t *chunk_words,
+                           uint64_t *chunks, uint64_t *chunk_fft_points);
 
 /* ---- One-shot products ---------------------------------------------------*/
 

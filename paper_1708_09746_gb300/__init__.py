@@ -14,7 +14,7 @@ import ctypes
 import os
 
 __all__ = [
-    "GF2XError", "load", "gf2x_strerror", "gf2x_out_words", "gf2x_fft_points",
+    "GF2XError", "load", "gf2x_strerror", "gf2x_out_words", "gf2x_fft_points", "gf2x_chunking",
     "gf2x_mul", "gf2x_mul_async", "gf2x_mul_host", "gf2x_plan_create",
     "gf2x_plan_workspace_bytes", "gf2x_plan_execute", "gf2x_plan_destroy",
     "gf2x_mul_batched", "gf2x_stage_basis_cvt64", "gf2x_stage_basis_cvt128",
@@ -59,6 +59,8 @@ _SIGS = {
     "gf2x_strerror": (ctypes.c_char_p, [_int]),
     "gf2x_out_words": (_u64, [_u64, _u64]),
     "gf2x_fft_points": (_u64, [_u64, _u64]),
+    "gf2x_chunking": (_int, [_u64, _u64, ctypes.POINTER(ctypes.c_uint64),
+                             ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "gf2x_mul": (_int, [_vp, _u64, _vp, _u64, _vp]),
     "gf2x_mul_async": (_int, [_vp, _u64, _vp, _u64, _vp, _vp]),
     "gf2x_mul_host": (_int, [_vp, _u64, _vp, _u64, _vp, _vp]),
@@ -154,6 +156,15 @@ def gf2x_out_words(na_bits, nb_bits):
 
 def gf2x_fft_points(na_bits, nb_bits):
     return int(load().gf2x_fft_points(na_bits, nb_bits))
+
+
+def gf2x_chunking(na_bits, nb_bits):
+    """(chunk words, chunks, points per chunk transform) of the one-shot calls'
+    chunked product; (0, 0, 0) when the product is one transform."""
+    L, C, N = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().gf2x_chunking(na_bits, nb_bits, ctypes.byref(L), ctypes.byref(C), ctypes.byref(N)),
+           "gf2x_chunking")
+    return int(L.value), int(C.value), int(N.value)
 
 
 def gf2x_mul(a, na_bits, b, nb_bits, out):

@@ -441,6 +441,26 @@ uint64_t gf2x_fft_points(uint64_t na_bits, uint64_t nb_bits) {
     return 1ull << log2_ceil(need);
 }
 
+int gf2x_chunking(uint64_t na_bits, uint64_t nb_bits, uint64_t *chunk_words, uint64_t *chunks,
+                  uint64_t *chunk_fft_points) {
+    if (!chunk_words || !chunks || !chunk_fft_points) return GF2X_EINVAL;
+    *chunk_words = *chunks = *chunk_fft_points = 0;
+    if (!na_bits || !nb_bits) return GF2X_OK;
+    const uint64_t na_w = words_of(na_bits), nb_w = words_of(nb_bits);
+    ChunkShape cs;
+    uint64_t yw;
+    if (chunk_shape(na_w, nb_w, &cs))
+        yw = nb_w;
+    else if (chunk_shape(nb_w, na_w, &cs))
+        yw = na_w;
+    else
+        return GF2X_OK;
+    *chunk_words = cs.L;
+    *chunks = cs.C;
+    *chunk_fft_points = 1ull << log2_ceil(std::max<uint64_t>(2, yw + cs.L - 1));
+    return GF2X_OK;
+}
+
 int gf2x_mul_async(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64_t nb_bits,
                    uint64_t *out, gf2x_stream_t stream) {
     try {

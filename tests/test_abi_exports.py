@@ -55,3 +55,18 @@ def test_host_helpers(lib):
     assert G.gf2x_fft_points(64, 64) == 2
     assert "invalid" in G.gf2x_strerror(-1)
     assert G.gf2x_strerror(12345) == "unknown status"
+
+
+def test_chunking_host_helper(lib):
+    # balanced and mildly unequal products run as one transform
+    assert G.gf2x_chunking(1 << 28, 1 << 28) == (0, 0, 0)
+    assert G.gf2x_chunking(64 * 2048, 64 * 513) == (0, 0, 0)   # 2 chunks only
+    # the c1 unequal workload: chunks of 2^10 words, 2^11-point transforms
+    assert G.gf2x_chunking(1 << 28, 1 << 16) == (1024, 4096, 2048)
+    assert G.gf2x_chunking(1 << 16, 1 << 28) == (1024, 4096, 2048)
+    # short operand below 512 words: chunks of 512 words
+    assert G.gf2x_chunking(64 * 5000 + 3, 1) == (512, 10, 512)
+    # at most 2^15 chunks: the chunk grows with the long operand
+    L, C, N = G.gf2x_chunking(1 << 33, 64)
+    assert C <= 1 << 15 and L * C >= (1 << 33) // 64 and L == 1 << 12 and N == 1 << 12
+    assert G.gf2x_chunking(0, 5) == (0, 0, 0)
