@@ -97,7 +97,7 @@ __device__ __forceinline__ void run_subpass(int G, uint4 *s, int c, int g, int r
     }
 }
 
-// Layers 3 .. 3+NR-1 of a contiguous tile (c = 0), NR = 1 or 2, with
+// Layers 3 .. 3+NR-1 of a contiguous tile (c = 0), NR = 1 .. 3, with
 // warp-uniform multipliers: a thread holds ONE 32-bit limb of the elements
 // that differ in index bits 3 .. 2+NR of a group of 2^(3+NR) elements, and the
 // 32 lanes of a warp are the 4 limbs x 8 elements (bits 0..2) of that group.
@@ -317,8 +317,9 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     // shuffle tables of the tile's multipliers for rows tb .. g-1 (all rows
     // when rows 0-2 run in registers with per-lane tables)
     const int tb = a.low3 ? 0 : uf, gt = g - tb;
-    // rows [uf, ul) run limb-wise (only the contiguous bottom pass: rows 3, 4)
-    const int ul = (c == 0 && uf == 3 && g >= 5) ? 5 : uf;
+    // rows [uf, ul) run limb-wise (only the contiguous bottom pass: rows 3-5,
+    // or 3-4 in a tile of 2^5 elements)
+    const int ul = (c == 0 && uf == 3 && g >= 5) ? min(g, 6) : uf;
     const uint32_t tile = 1u << (g + c);
     const int NB = a.nbuf;
     uint4 *const buf0 = reinterpret_cast<uint4 *>(smem);  // buffer b at buf0 + b * tile
@@ -432,8 +433,11 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
                 run_subpass<false>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab_u, a.d_shfl);
                 __syncthreads();
             }
-            if (ul > uf && a.g_f > uf) {  // rows 3, 4 limb-wise
-                if (a.g_f >= 5)
+            if (ul > uf && a.g_f > uf) {  // rows 3 .. min(g_f, ul) - 1 limb-wise
+                const int nr = min(a.g_f, ul) - uf;
+                if (nr >= 3)
+                    limb_subpass<3, false>(s, g, uf, ctab_u, a.d_shfl);
+                else if (nr == 2)
                     limb_subpass<2, false>(s, g, uf, ctab_u, a.d_shfl);
                 else
                     limb_subpass<1, false>(s, g, uf, ctab_u, a.d_shfl);
@@ -466,8 +470,11 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
                     __syncthreads();
                 }
             }
-            if (ul > uf) {  // rows 3, 4 limb-wise
-                limb_subpass<2, true>(s, g, uf, ctab_u, a.d_shfl);
+            if (ul > uf) {  // rows 3 .. ul - 1 limb-wise
+                if (ul - uf >= 3)
+                    limb_subpass<3, true>(s, g, uf, ctab_u, a.d_shfl);
+                else
+                    limb_subpass<2, true>(s, g, uf, ctab_u, a.d_shfl);
                 __syncthreads();
             }
             for (int r_lo = ul; r_lo < g; r_lo += 3) {
