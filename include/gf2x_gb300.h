@@ -30,6 +30,13 @@
  *  - `out` must not overlap `a` or `b` (GF2X_EINVAL).
  *  - Asynchronous calls enqueue kernels on the caller's stream (0 = the
  *    legacy default stream) and return without waiting.
+ *  - Device-side failures: every wait inside a kernel is bounded; a wait that
+ *    runs out ends the kernel early and records GF2X_ETIMEOUT in a status word
+ *    of the call that launched it (its output is then undefined).  Synchronous
+ *    calls return it themselves; the asynchronous calls made on one stream
+ *    share that stream's word, which gf2x_stream_status reads; a batch and
+ *    each server request have their own (gf2x_batch_status,
+ *    gf2x_server_wait).
  *  - Every call returns an int status; no C++ exception crosses this ABI.
  *  - Sizes: operands up to 2^33 bits each (N <= 2^28 FFT points); larger
  *    sizes give GF2X_EINVAL.
@@ -57,7 +64,8 @@ enum {
     GF2X_EINVAL = -1,   /* bad argument (size, null, host pointer, overlap) */
     GF2X_ENOMEM = -2,   /* device or host allocation failed */
     GF2X_ECUDA = -3,    /* a CUDA call or kernel launch failed, or no GPU */
-    GF2X_ETIMEOUT = -4, /* a bounded wait ran out (server API) */
+    GF2X_ETIMEOUT = -4, /* a bounded wait ran out (a host wait of the server
+                           API, or a device wait inside a kernel) */
     GF2X_EBUSY = -5     /* a resource is in use (server slots / budget) */
 };
 
@@ -207,6 +215,11 @@ GF2X_API int gf2x_batch_execute(gf2x_batch *batch, const uint64_t *const *a,
                                 gf2x_stream_t stream);
 GF2X_API int gf2x_batch_destroy(gf2x_batch *batch);
 
+/* Waits for the batch's last execution and returns GF2X_ETIMEOUT if a bounded
+ * device wait in it ran out (its outputs are then undefined), else GF2X_OK
+ * (GF2X_OK too if it was never executed). */
+GF2X_API int gf2x_batch_status(gf2x_batch *batch);
+
 /* ---- Serving ----------------------------------------------------------------
  * A server runs products submitted at any time.  A worker thread admits the
  * queued requests in arrival order as execution slots (CUDA streams, at most
@@ -334,6 +347,23 @@ GF2X_API int gf2x_probe_pipes(double *shfl_per_clk_sm, double *xor_per_clk_sm,
 GF2X_API int gf2x_mul_noalloc(const uint64_t *a, uint64_t na_bits,
                               const uint64_t *b, uint64_t nb_bits,
                               uint64_t *out, gf2x_stream_t stream);
+
+/* ---- Device-side failures ------------------------------------------------*/
+
+/* Waits for `stream` and returns the status of the asynchronous calls made
+ * on it since the last gf2x_stream_status of that stream (gf2x_mul_async,
+ * gf2x_plan_execute, gf2x_mul_batched): GF2X_ETIMEOUT if a bounded device wait
+ * in one of them ran out, else GF2X_OK; the stream's status is then cleared.
+ * The library keeps one status word per stream it has seen (up to 512 per
+ * device; the calls on further streams share word 0 of the device). */
+GF2X_API int gf2x_stream_status(gf2x_stream_t stream);
+
+/* For tests of the timeout path: every bounded device wait of the kernels
+ * launched from now on gives up after `spins` attempts (0: at once, without
+ * waiting); a negative value restores the default bound (2^24 attempts).  The
+ * kernels still let every copy they started land before they exit.  Process-
+ * wide; not for production use. */
+GF2X_API int gf2x_debug_set_wait_spins(int64_t spins);
 
 /* Releases the per-device tables and cached plans of this library. */
 GF2X_API int gf2x_shutdown(void);

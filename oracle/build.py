@@ -3,6 +3,7 @@
 TEST INFRASTRUCTURE ONLY: the product path never loads this library.
 """
 import os
+import platform
 import subprocess
 import sys
 
@@ -18,14 +19,21 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
         return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-o", tmp, SRC]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        # OpenMP is optional: fall back to a serial build of the same source.
-        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, SRC]
+    # The PMULL form of clmul64 exists only for aarch64 compilers; OpenMP is
+    # optional.  Each variant is tried in turn, the plainest last.
+    pmull = ["-DGF2O_PMULL"] if platform.machine().lower() in ("aarch64", "arm64") else []
+    variants = [pmull + ["-fopenmp"], ["-fopenmp"], []]
+    if not pmull:
+        variants = variants[1:]
+    err = ""
+    for extra in variants:
+        cmd = ["gcc", "-O2", "-fPIC", "-shared"] + extra + ["-o", tmp, SRC]
         r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError("oracle build failed:\n" + r.stderr)
+        if r.returncode == 0:
+            break
+        err = r.stderr
+    else:
+        raise RuntimeError("oracle build failed:\n" + err)
     os.replace(tmp, LIB)
     return LIB
 

@@ -8,7 +8,13 @@
  * (Sec. 2.1 and Alg. 5 of the paper: c(x) = a(x) * b(x) in GF(2)[x]), written
  * out without any FFT:
  *
- *   clmul64        the 64x64 -> 128-bit carry-less product, bit by bit.
+ *   clmul64        the 64x64 -> 128-bit carry-less product, bit by bit (the
+ *                  definition; the pin for the two faster forms below).
+ *   clmul64_win4   the same product by 4-bit windows of y (a 16-entry table
+ *                  of x times every 4-bit polynomial), portable C.
+ *   clmul64_pmull  the same product by the aarch64 PMULL instruction, built
+ *                  only where the compiler targets aarch64 and used only where
+ *                  the CPU reports it; tests cross-check it against clmul64.
  *   mul_schoolbook the word-level schoolbook product built on clmul64.
  *   mul_karatsuba  Karatsuba's three-product recursion over the schoolbook,
  *                  optionally OpenMP-parallel at the top levels.
@@ -20,15 +26,23 @@
  * Packing (reading of Sec. 2.1, which fixes only the coefficient order): bit i
  * of 64-bit word j is the coefficient of x^(64 j + i) (little-endian words).
  *
- * Built with plain gcc, no intrinsics, so it behaves the same on x86_64 and
- * aarch64 hosts.  Parity status: pinned (brute force, closed forms,
- * invariants; see tests/test_oracle_product.py).
+ * Built with plain gcc.  The only machine-specific code is the optional PMULL
+ * form (compiled with -DGF2O_PMULL on aarch64 only); the products are the same
+ * on x86_64 and aarch64 hosts.  Parity status: pinned (brute force, closed
+ * forms, invariants; see tests/test_oracle_product.py).
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
+#endif
+#if defined(GF2O_PMULL) && defined(__aarch64__)
+#include <arm_neon.h>
+#include <sys/auxv.h>
+#ifndef HWCAP_PMULL
+#define HWCAP_PMULL (1 << 4)
+#endif
 #endif
 
 /* 64x64 carry-less multiply, shift-and-add over the bits of y. */
@@ -45,20 +59,159 @@ void gf2o_clmul64(uint64_t x, uint64_t y, uint64_t *lo, uint64_t *hi)
     *hi = h;
 }
 
-/* out[0 .. na+nb) = a[0..na) * b[0..nb), words; out must not alias a or b. */
+/* The same product by 4-bit windows of y from the top: acc = acc * x^4 +
+ * T[nibble], T[t] = x * t(x) for the 16 polynomials t of degree < 4. */
+void gf2o_clmul64_win4(uint64_t x, uint64_t y, uint64_t *lo, uint64_t *hi)
+{
+    uint64_t tl[16], th[16];
+    tl[0] = 0;
+    th[0] = 0;
+    for (int t = 1; t < 16; t++) {
+        uint64_t l = 0, h = 0;
+        for (int i = 0; i < 4; i++) {
+            if ((t >> i) & 1) {
+                l ^= x << i;
+                if (i) h ^= x >> (64 - i);
+            }
+        }
+        tl[t] = l;
+        th[t] = h;
+    }
+    uint64_t l = 0, h = 0;
+    for (int k = 60; k >= 0; k -= 4) {
+        unsigned t = (unsigned)(y >> k) & 15u;
+        h = (h << 4) | (l >> 60);
+        l <<= 4;
+        l ^= tl[t];
+        h ^= th[t];
+    }
+    *lo = l;
+    *hi = h;
+}
+
+#if defined(GF2O_PMULL) && defined(__aarch64__)
+__attribute__((target("+crypto")))
+static void clmul64_pmull(uint64_t x, uint64_t y, uint64_t *lo, uint64_t *hi)
+{
+    poly128_t p = vmull_p64((poly64_t)x, (poly64_t)y);
+    uint64x2_t v = vreinterpretq_u64_p128(p);
+    *lo = vgetq_lane_u64(v, 0);
+    *hi = vgetq_lane_u64(v, 1);
+}
+#endif
+
+typedef void (*clmul_fn)(uint64_t, uint64_t, uint64_t *, uint64_t *);
+
+/* The fastest form this host has: 1 = PMULL, 0 = 4-bit windows. */
+static clmul_fn pick_clmul(int *kind)
+{
+#if defined(GF2O_PMULL) && defined(__aarch64__)
+    if (getauxval(AT_HWCAP) & HWCAP_PMULL) {
+        *kind = 1;
+        return clmul64_pmull;
+    }
+#endif
+    *kind = 0;
+    return gf2o_clmul64_win4;
+}
+
+static clmul_fn g_clmul = 0;
+static int g_clmul_kind = -1;
+
+static clmul_fn clmul_fast(void)
+{
+    if (!g_clmul) {
+        int k = 0;
+        clmul_fn f = pick_clmul(&k);
+        g_clmul_kind = k;
+        g_clmul = f;
+    }
+    return g_clmul;
+}
+
+/* Which form the schoolbook, Karatsuba and product-word routines use. */
+int gf2o_clmul_kind(void)
+{
+    clmul_fast();
+    return g_clmul_kind;
+}
+
+/* The product by that form (exported so that tests can check it against the
+ * bit-by-bit definition). */
+void gf2o_clmul64_fast(uint64_t x, uint64_t y, uint64_t *lo, uint64_t *hi)
+{
+    clmul_fast()(x, y, lo, hi);
+}
+
+#if defined(GF2O_PMULL) && defined(__aarch64__)
+/* Schoolbook rows with the PMULL product inline. */
+__attribute__((target("+crypto")))
+static void schoolbook_pmull(const uint64_t *a, int64_t na, const uint64_t *b,
+                             int64_t nb, uint64_t *out)
+{
+    for (int64_t i = 0; i < na; i++) {
+        if (!a[i]) continue;
+        const poly64_t x = (poly64_t)a[i];
+        for (int64_t j = 0; j < nb; j++) {
+            uint64x2_t v = vreinterpretq_u64_p128(vmull_p64(x, (poly64_t)b[j]));
+            out[i + j] ^= vgetq_lane_u64(v, 0);
+            out[i + j + 1] ^= vgetq_lane_u64(v, 1);
+        }
+    }
+}
+#endif
+
+/* Schoolbook rows by 4-bit windows, the table of a[i] built once per row. */
+static void schoolbook_win4(const uint64_t *a, int64_t na, const uint64_t *b,
+                            int64_t nb, uint64_t *out)
+{
+    uint64_t tl[16], th[16];
+    for (int64_t i = 0; i < na; i++) {
+        const uint64_t x = a[i];
+        if (!x) continue;
+        tl[0] = 0;
+        th[0] = 0;
+        for (int t = 1; t < 16; t++) {
+            uint64_t l = 0, h = 0;
+            for (int q = 0; q < 4; q++) {
+                if ((t >> q) & 1) {
+                    l ^= x << q;
+                    if (q) h ^= x >> (64 - q);
+                }
+            }
+            tl[t] = l;
+            th[t] = h;
+        }
+        for (int64_t j = 0; j < nb; j++) {
+            const uint64_t y = b[j];
+            uint64_t l = 0, h = 0;
+            for (int k = 60; k >= 0; k -= 4) {
+                unsigned t = (unsigned)(y >> k) & 15u;
+                h = (h << 4) | (l >> 60);
+                l <<= 4;
+                l ^= tl[t];
+                h ^= th[t];
+            }
+            out[i + j] ^= l;
+            out[i + j + 1] ^= h;
+        }
+    }
+}
+
+/* out[0 .. na+nb) = a[0..na) * b[0..nb), words; out must not alias a or b.
+ * Each term a_i b_j x^(64(i+j)) is one carry-less word product (the fastest
+ * form the host has, see gf2o_clmul_kind). */
 void gf2o_mul_schoolbook(const uint64_t *a, int64_t na, const uint64_t *b,
                          int64_t nb, uint64_t *out)
 {
     memset(out, 0, (size_t)(na + nb) * sizeof(uint64_t));
-    for (int64_t i = 0; i < na; i++) {
-        if (!a[i]) continue;
-        for (int64_t j = 0; j < nb; j++) {
-            uint64_t lo, hi;
-            gf2o_clmul64(a[i], b[j], &lo, &hi);
-            out[i + j] ^= lo;
-            out[i + j + 1] ^= hi;
-        }
+#if defined(GF2O_PMULL) && defined(__aarch64__)
+    if (gf2o_clmul_kind() == 1) {
+        schoolbook_pmull(a, na, b, nb, out);
+        return;
     }
+#endif
+    schoolbook_win4(a, na, b, nb, out);
 }
 
 #define KARA_BASE 32
@@ -81,27 +234,26 @@ static void kara_rec(const uint64_t *a, const uint64_t *b, int64_t n,
     }
     uint64_t *lo = out, *hiw = out + 2 * h; /* a0 b0 and a1 b1 */
     if (par_depth > 0) {
-        /* Three independent sub-products; each gets its own scratch. */
+        /* Three independent sub-products as OpenMP tasks (the caller runs
+         * the top call inside a parallel region); each has its own scratch. */
         uint64_t *t1 = (uint64_t *)malloc((size_t)4 * h * sizeof(uint64_t));
         uint64_t *t2 = (uint64_t *)malloc((size_t)4 * h * sizeof(uint64_t));
         uint64_t *t3 = (uint64_t *)malloc((size_t)4 * h * sizeof(uint64_t));
 #ifdef _OPENMP
-#pragma omp parallel sections
+#pragma omp task
 #endif
-        {
+        kara_rec(a0, b0, h, lo, t1, par_depth - 1);
 #ifdef _OPENMP
-#pragma omp section
+#pragma omp task
 #endif
-            kara_rec(a0, b0, h, lo, t1, par_depth - 1);
+        kara_rec(a1, b1, h, hiw, t2, par_depth - 1);
 #ifdef _OPENMP
-#pragma omp section
+#pragma omp task
 #endif
-            kara_rec(a1, b1, h, hiw, t2, par_depth - 1);
+        kara_rec(sa, sb, h, mid, t3, par_depth - 1);
 #ifdef _OPENMP
-#pragma omp section
+#pragma omp taskwait
 #endif
-            kara_rec(sa, sb, h, mid, t3, par_depth - 1);
-        }
         free(t1);
         free(t2);
         free(t3);
@@ -137,7 +289,16 @@ int gf2o_mul_karatsuba(const uint64_t *a, int64_t na, const uint64_t *b,
     }
     memcpy(pa, a, (size_t)na * sizeof(uint64_t));
     memcpy(pb, b, (size_t)nb * sizeof(uint64_t));
-    kara_rec(pa, pb, p, po, tmp, par_depth);
+    clmul_fast(); /* pick the form before any thread uses it */
+    if (par_depth > 0) {
+#ifdef _OPENMP
+#pragma omp parallel
+#pragma omp single
+#endif
+        kara_rec(pa, pb, p, po, tmp, par_depth);
+    } else {
+        kara_rec(pa, pb, p, po, tmp, 0);
+    }
     memcpy(out, po, (size_t)(na + nb) * sizeof(uint64_t));
     free(pa); free(pb); free(po); free(tmp);
     return 0;
@@ -204,19 +365,20 @@ int gf2o_num_threads(void)
 uint64_t gf2o_product_word(const uint64_t *a, int64_t na, const uint64_t *b,
                            int64_t nb, int64_t j)
 {
+    clmul_fn mul = clmul_fast();
     uint64_t acc = 0;
     int64_t i0 = j - (nb - 1);
     if (i0 < 0) i0 = 0;
     for (int64_t i = i0; i <= j && i < na; i++) {
         uint64_t lo, hi;
-        gf2o_clmul64(a[i], b[j - i], &lo, &hi);
+        mul(a[i], b[j - i], &lo, &hi);
         acc ^= lo;
     }
     i0 = j - 1 - (nb - 1);
     if (i0 < 0) i0 = 0;
     for (int64_t i = i0; i <= j - 1 && i < na; i++) {
         uint64_t lo, hi;
-        gf2o_clmul64(a[i], b[j - 1 - i], &lo, &hi);
+        mul(a[i], b[j - 1 - i], &lo, &hi);
         acc ^= hi;
     }
     return acc;

@@ -38,6 +38,9 @@ def lib():
         L.gf2o_product_word.argtypes = [u64p, ctypes.c_int64, u64p, ctypes.c_int64,
                                         ctypes.c_int64]
         L.gf2o_product_word.restype = ctypes.c_uint64
+        L.gf2o_clmul64_win4.argtypes = [ctypes.c_uint64, ctypes.c_uint64, u64p, u64p]
+        L.gf2o_clmul64_fast.argtypes = [ctypes.c_uint64, ctypes.c_uint64, u64p, u64p]
+        L.gf2o_clmul_kind.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -67,6 +70,26 @@ def clmul64(x, y):
     hi = ctypes.c_uint64()
     lib().gf2o_clmul64(int(x), int(y), ctypes.byref(lo), ctypes.byref(hi))
     return lo.value, hi.value
+
+
+def clmul64_win4(x, y):
+    lo = ctypes.c_uint64()
+    hi = ctypes.c_uint64()
+    lib().gf2o_clmul64_win4(int(x), int(y), ctypes.byref(lo), ctypes.byref(hi))
+    return lo.value, hi.value
+
+
+def clmul64_fast(x, y):
+    """The form the product routines use (PMULL where the host has it)."""
+    lo = ctypes.c_uint64()
+    hi = ctypes.c_uint64()
+    lib().gf2o_clmul64_fast(int(x), int(y), ctypes.byref(lo), ctypes.byref(hi))
+    return lo.value, hi.value
+
+
+def clmul_kind():
+    """'pmull' or 'win4': the carry-less multiply the product routines use."""
+    return "pmull" if lib().gf2o_clmul_kind() == 1 else "win4"
 
 
 def mul_schoolbook(a, na_bits, b, nb_bits):
@@ -111,7 +134,11 @@ def mul(a, na_bits, b, nb_bits, threads=None):
     if threads is None:
         threads = lib().gf2o_num_threads()
     if threads > 1 and nw >= 4096:
-        depth = 2 if threads < 16 else 3
+        # enough tasks (3^depth) to keep every thread busy, and no deeper than
+        # the recursion itself (halving down to the 32-word base case)
+        depth = 1
+        while 3 ** depth < 4 * threads and (nw >> (depth + 1)) >= 64:
+            depth += 1
     return mul_karatsuba(a, na_bits, b, nb_bits, par_depth=depth)
 
 

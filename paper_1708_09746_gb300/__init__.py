@@ -24,6 +24,7 @@ __all__ = [
     "gf2x_batch_create", "gf2x_batch_workspace_bytes", "gf2x_batch_execute", "gf2x_batch_destroy",
     "gf2x_server_create", "gf2x_server_submit", "gf2x_server_wait", "gf2x_server_stats",
     "gf2x_server_reset_stats", "gf2x_server_destroy", "gf2x_probe_pipes", "LIB_PATH",
+    "gf2x_stream_status", "gf2x_batch_status", "gf2x_debug_set_wait_spins",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -101,6 +102,9 @@ _SIGS = {
     "gf2x_tune_set": (_int, [_u64, _u64, ctypes.POINTER(gf2x_tune_t)]),
     "gf2x_tune_save": (_int, [ctypes.c_char_p]),
     "gf2x_tune_load": (_int, [ctypes.c_char_p]),
+    "gf2x_stream_status": (_int, [_vp]),
+    "gf2x_batch_status": (_int, [_vp]),
+    "gf2x_debug_set_wait_spins": (_int, [ctypes.c_int64]),
 }
 
 
@@ -397,3 +401,21 @@ def gf2x_server_reset_stats(server):
 
 def gf2x_server_destroy(server):
     _check(load().gf2x_server_destroy(server), "gf2x_server_destroy")
+
+
+def gf2x_stream_status(stream=None):
+    """Waits for `stream`; raises GF2XError(GF2X_ETIMEOUT) if a bounded device
+    wait of an asynchronous call on it ran out since the last check."""
+    _check(load().gf2x_stream_status(_stream(stream)), "gf2x_stream_status")
+
+
+def gf2x_batch_status(batch):
+    """Waits for the batch's last execution; raises GF2XError(GF2X_ETIMEOUT)
+    if a bounded device wait in it ran out."""
+    _check(load().gf2x_batch_status(batch), "gf2x_batch_status")
+
+
+def gf2x_debug_set_wait_spins(spins):
+    """Bound of the kernels' device waits for tests of the timeout path
+    (0: give up at once; negative: the default)."""
+    _check(load().gf2x_debug_set_wait_spins(int(spins)), "gf2x_debug_set_wait_spins")

@@ -23,9 +23,21 @@ using namespace gf2x;
 namespace {
 
 // ---- Per-device context: the size-independent tables, uploaded once. ------
+//
+// Status words: a kernel that gives up a bounded wait writes GF2X_ETIMEOUT to
+// the status word it was launched with.  Each device has one array of
+// kStatusWords such words: word 0 belongs to the stage entry points; a
+// synchronous call (gf2x_mul, gf2x_mul_host) takes a free word for its own
+// duration; the asynchronous calls made on one stream share a word of that
+// stream (read and cleared by gf2x_stream_status); each server slot owns one.
+// So a timeout is reported to the call, stream or request that caused it.
+constexpr int kStatusWords = 1024;
+
 struct DeviceCtx {
     DevTables *tables = nullptr;
-    int *status = nullptr;  // device status word of the pipelined kernels
+    int *status = nullptr;  // kStatusWords device status words
+    std::vector<int> free_words;                // unused word indices (>= 1)
+    std::map<cudaStream_t, int> stream_words;   // stream -> its word
     // Workspace pool: keeps its memory mapped between products (release
     // threshold at the maximum), so that a product does not map and unmap the
     // pages of its workspace every time.
@@ -66,7 +78,8 @@ int get_tables(const DevTables **out) {
             return GF2X_ECUDA;
         }
         int *st = nullptr;
-        if (cudaMalloc(&st, sizeof(int)) != cudaSuccess || cudaMemset(st, 0, sizeof(int)) != cudaSuccess) {
+        if (cudaMalloc(&st, kStatusWords * sizeof(int)) != cudaSuccess ||
+            cudaMemset(st, 0, kStatusWords * sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(d);
             if (st) cudaFree(st);
@@ -74,6 +87,9 @@ int get_tables(const DevTables **out) {
         }
         c.tables = d;
         c.status = st;
+        c.free_words.clear();
+        for (int i = kStatusWords - 1; i >= 1; i--) c.free_words.push_back(i);
+        c.stream_words.clear();
     }
     *out = c.tables;
     return GF2X_OK;
@@ -131,7 +147,8 @@ void ws_free(void *p, cudaStream_t s) {
     if (p) cudaFreeAsync(p, s);
 }
 
-// Device status word of the current device (valid after get_tables).
+// Word 0 of the current device: the stage entry points' status word (valid
+// after get_tables).
 int *device_status() {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -139,17 +156,78 @@ int *device_status() {
     return g_ctx[dev].status;
 }
 
-// Reads and clears the device status word (synchronises the device).
-int take_device_status() {
-    int *st = device_status();
+// Reads and clears one status word.  The caller has waited for the work that
+// writes it.
+int read_clear_status(int *st) {
     if (!st) return GF2X_OK;
     int v = 0;
-    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&v, st, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    if (cudaMemcpy(&v, st, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
         cudaGetLastError();
         return GF2X_ECUDA;
     }
-    if (v) cudaMemset(st, 0, sizeof(int));
+    if (v && cudaMemset(st, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return GF2X_ECUDA;
+    }
     return v;
+}
+
+// Reads and clears word 0 after the whole device has finished.
+int take_device_status() {
+    int *st = device_status();
+    if (!st) return GF2X_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return GF2X_ECUDA;
+    }
+    return read_clear_status(st);
+}
+
+// A free status word of the current device for one call (GF2X_EBUSY when all
+// are in use); give it back with give_status_word once its work has finished.
+int take_status_word(int **w) {
+    const DevTables *T;
+    int rc = get_tables(&T);
+    if (rc) return rc;
+    int dev = 0;
+    if ((rc = current_device(&dev))) return rc;
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    DeviceCtx &c = g_ctx[dev];
+    if (c.free_words.empty()) return GF2X_EBUSY;
+    *w = c.status + c.free_words.back();
+    c.free_words.pop_back();
+    return GF2X_OK;
+}
+
+void give_status_word(int *w) {
+    if (!w) return;
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    for (auto &kv : g_ctx) {
+        DeviceCtx &c = kv.second;
+        if (c.status && w > c.status && w < c.status + kStatusWords) {
+            c.free_words.push_back((int)(w - c.status));
+            return;
+        }
+    }
+}
+
+// The status word of the asynchronous calls on stream s of the current device
+// (taken on first use and kept; when no word is free, word 0).
+int *stream_status_word(cudaStream_t s) {
+    const DevTables *T;
+    if (get_tables(&T)) return nullptr;
+    int dev = 0;
+    if (current_device(&dev)) return nullptr;
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    DeviceCtx &c = g_ctx[dev];
+    auto it = c.stream_words.find(s);
+    if (it != c.stream_words.end()) return c.status + it->second;
+    // keep half the words for the synchronous calls and the server slots
+    if ((int)c.stream_words.size() >= kStatusWords / 2 || c.free_words.empty()) return c.status;
+    const int i = c.free_words.back();
+    c.free_words.pop_back();
+    c.stream_words[s] = i;
+    return c.status + i;
 }
 
 int check_launch() {
@@ -157,7 +235,8 @@ int check_launch() {
     return e == cudaSuccess ? GF2X_OK : GF2X_ECUDA;
 }
 
-// Device (or managed) memory?  A null pointer is accepted only for size 0.
+// Device memory of the current device, or managed memory?  A null pointer is
+// accepted only for size 0.
 int check_dev_ptr(const void *p, size_t bytes) {
     if (bytes == 0) return GF2X_OK;
     if (!p) return GF2X_EINVAL;
@@ -167,8 +246,16 @@ int check_dev_ptr(const void *p, size_t bytes) {
         cudaGetLastError();
         return GF2X_EINVAL;
     }
-    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return GF2X_EINVAL;
-    return GF2X_OK;
+    if (at.type == cudaMemoryTypeManaged) return GF2X_OK;
+    if (at.type != cudaMemoryTypeDevice) return GF2X_EINVAL;
+    // device memory of another GPU: the kernels run on the current device and
+    // would reach it only through peer access, so it is refused
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return GF2X_ECUDA;
+    }
+    return at.device == dev ? GF2X_OK : GF2X_EINVAL;
 }
 
 bool overlap(const void *a, size_t na, const void *b, size_t nb) {
@@ -295,12 +382,13 @@ int plan_init(gf2x_plan *p, uint64_t na_bits, uint64_t nb_bits, const PlanTune *
 
 // Alg. 5, stage after stage, on `s`, with the library's tables.
 int plan_run(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out, void *ws,
-             cudaStream_t s, cudaEvent_t b_ready = nullptr, const OutputDrain *drain = nullptr) {
+             cudaStream_t s, int *st, cudaEvent_t b_ready = nullptr,
+             const OutputDrain *drain = nullptr) {
     const DevTables *T;
     int rc = get_tables(&T);
     if (rc) return rc;
     StageTimer tm(s);
-    rc = plan_run_core(p, a, b, out, ws, s, T, device_status(), &tm, b_ready, drain);
+    rc = plan_run_core(p, a, b, out, ws, s, T, st, &tm, b_ready, drain);
     return rc ? GF2X_ECUDA : GF2X_OK;
 }
 
@@ -359,7 +447,7 @@ int check_operands(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint6
 // Unbalanced operands: the product by chunks of the long operand against one
 // transform of the short one (plan_run_chunked).
 int mul_chunked(const uint64_t *x, uint64_t x_bits, const uint64_t *y, uint64_t y_bits,
-                uint64_t *out, const ChunkShape &cs, cudaStream_t s) {
+                uint64_t *out, const ChunkShape &cs, cudaStream_t s, int *st) {
     std::shared_ptr<gf2x_plan> pc;
     int rc = cached_plan(y_bits, 64 * cs.L, &pc);
     if (rc) return rc;
@@ -368,25 +456,25 @@ int mul_chunked(const uint64_t *x, uint64_t x_bits, const uint64_t *y, uint64_t 
     void *ws = nullptr;
     if ((rc = ws_alloc(&ws, chunked_ws_bytes(pc.get(), cs.C), s))) return rc;
     StageTimer tm(s);
-    rc = plan_run_chunked(pc.get(), cs, x, x_bits, y, y_bits, out, ws, s, T, device_status(), &tm);
+    rc = plan_run_chunked(pc.get(), cs, x, x_bits, y, y_bits, out, ws, s, T, st, &tm);
     ws_free(ws, s);
     if (rc) return GF2X_ECUDA;
     return check_launch();
 }
 
 int mul_on_stream(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64_t nb_bits,
-                  uint64_t *out, cudaStream_t s) {
+                  uint64_t *out, cudaStream_t s, int *st) {
     ChunkShape cs;
     if (chunk_shape(words_of(na_bits), words_of(nb_bits), &cs))
-        return mul_chunked(a, na_bits, b, nb_bits, out, cs, s);
+        return mul_chunked(a, na_bits, b, nb_bits, out, cs, s, st);
     if (chunk_shape(words_of(nb_bits), words_of(na_bits), &cs))
-        return mul_chunked(b, nb_bits, a, na_bits, out, cs, s);
+        return mul_chunked(b, nb_bits, a, na_bits, out, cs, s, st);
     std::shared_ptr<gf2x_plan> p;
     int rc = cached_plan(na_bits, nb_bits, &p);
     if (rc) return rc;
     void *ws = nullptr;
     if ((rc = ws_alloc(&ws, p->ws_bytes, s))) return rc;
-    rc = plan_run(p.get(), a, b, out, ws, s);
+    rc = plan_run(p.get(), a, b, out, ws, s, st);
     ws_free(ws, s);
     if (rc == GF2X_OK) rc = check_launch();
     return rc;
@@ -398,7 +486,9 @@ int mul_on_stream(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64
 namespace gf2x {
 namespace api {
 int tables(const DevTables **T) { return get_tables(T); }
-int *status_word() { return device_status(); }
+int *stream_status(cudaStream_t s) { return stream_status_word(s); }
+int take_status(int **w) { return take_status_word(w); }
+void give_status(int *w) { give_status_word(w); }
 int plan_for(uint64_t na_bits, uint64_t nb_bits, std::shared_ptr<gf2x_plan> *p) {
     return cached_plan(na_bits, nb_bits, p);
 }
@@ -411,7 +501,7 @@ int ws_alloc(void **p, size_t bytes, cudaStream_t s) { return ::ws_alloc(p, byte
 void ws_free(void *p, cudaStream_t s) { ::ws_free(p, s); }
 int run_one(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out, void *ws,
             cudaStream_t s) {
-    return plan_run(p, a, b, out, ws, s);
+    return plan_run(p, a, b, out, ws, s, stream_status_word(s));
 }
 }  // namespace api
 }  // namespace gf2x
@@ -467,7 +557,10 @@ int gf2x_mul_async(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint6
         int rc = check_operands(a, na_bits, b, nb_bits, out);
         if (rc) return rc;
         if (!na_bits || !nb_bits) return GF2X_OK;
-        return mul_on_stream(a, na_bits, b, nb_bits, out, reinterpret_cast<cudaStream_t>(stream));
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        int *st = stream_status_word(s);
+        if (!st) return GF2X_ECUDA;
+        return mul_on_stream(a, na_bits, b, nb_bits, out, s, st);
     } catch (const std::bad_alloc &) {
         return GF2X_ENOMEM;
     } catch (...) {
@@ -477,13 +570,32 @@ int gf2x_mul_async(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint6
 
 int gf2x_mul(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64_t nb_bits,
              uint64_t *out) {
-    int rc = gf2x_mul_async(a, na_bits, b, nb_bits, out, nullptr);
-    if (rc) return rc;
-    if (cudaStreamSynchronize(0) != cudaSuccess) {
-        cudaGetLastError();
+    try {
+        int rc = check_operands(a, na_bits, b, nb_bits, out);
+        if (rc) return rc;
+        if (!na_bits || !nb_bits) return GF2X_OK;
+        // a status word of this call's own, so that a timeout is reported
+        // here and nowhere else
+        int *st = nullptr;
+        if ((rc = take_status_word(&st))) return rc;
+        if (cudaMemsetAsync(st, 0, sizeof(int), 0) != cudaSuccess) {
+            cudaGetLastError();
+            give_status_word(st);
+            return GF2X_ECUDA;
+        }
+        rc = mul_on_stream(a, na_bits, b, nb_bits, out, nullptr, st);
+        if (cudaStreamSynchronize(0) != cudaSuccess) {
+            cudaGetLastError();
+            rc = GF2X_ECUDA;
+        }
+        const int ds = read_clear_status(st);
+        give_status_word(st);
+        return rc ? rc : ds;
+    } catch (const std::bad_alloc &) {
+        return GF2X_ENOMEM;
+    } catch (...) {
         return GF2X_ECUDA;
     }
-    return take_device_status();
 }
 
 int gf2x_mul_host(const uint64_t *a_host, uint64_t na_bits, const uint64_t *b_host,
@@ -523,6 +635,13 @@ int gf2x_mul_host(const uint64_t *a_host, uint64_t na_bits, const uint64_t *b_ho
             return GF2X_ECUDA;
         }
         cudaEvent_t alloc_done = ev[kPieces], b_ready = ev[kPieces + 1], drained = ev[kPieces + 2];
+        int *st = nullptr;
+        if ((rc = take_status_word(&st))) {
+            for (auto &x : ev) cudaEventDestroy(x);
+            ws_free(buf, s);
+            return rc;
+        }
+        cudaMemsetAsync(st, 0, sizeof(int), s);
         // a first, alone on the link; b after it, while a is being processed
         cudaMemcpyAsync(da, a_host, ba, cudaMemcpyHostToDevice, s);
         cudaEventRecord(alloc_done, s);
@@ -530,17 +649,19 @@ int gf2x_mul_host(const uint64_t *a_host, uint64_t na_bits, const uint64_t *b_ho
         cudaMemcpyAsync(db, b_host, bb, cudaMemcpyHostToDevice, cs);
         cudaEventRecord(b_ready, cs);
         const OutputDrain drain{cs, out_host, kPieces, ev};
-        rc = plan_run(p.get(), da, db, dout, buf, s, b_ready, &drain);
+        rc = plan_run(p.get(), da, db, dout, buf, s, st, b_ready, &drain);
         cudaEventRecord(drained, cs);
         cudaStreamWaitEvent(s, drained, 0);  // the copies have read the buffer
         ws_free(buf, s);
         cudaError_t e = cudaStreamSynchronize(s);
         for (auto &x : ev) cudaEventDestroy(x);
+        const int ds = e == cudaSuccess ? read_clear_status(st) : GF2X_ECUDA;
+        give_status_word(st);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return GF2X_ECUDA;
         }
-        return rc;
+        return rc ? rc : ds;
     } catch (const std::bad_alloc &) {
         return GF2X_ENOMEM;
     } catch (...) {
@@ -603,7 +724,10 @@ int gf2x_plan_execute(gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64
             }
             ws = p->owned_ws;
         }
-        return plan_run(p, a, b, out, ws, reinterpret_cast<cudaStream_t>(stream));
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        int *st = stream_status_word(s);
+        if (!st) return GF2X_ECUDA;
+        return plan_run(p, a, b, out, ws, s, st);
     } catch (...) {
         return GF2X_ECUDA;
     }
@@ -798,18 +922,24 @@ int gf2x_autotune(uint64_t na_bits, uint64_t nb_bits, int reps, gf2x_tune_t *bes
         cudaMemset(db, 0xa5, bb);
         cudaStream_t s = nullptr;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
+        int *st = nullptr;
+        if ((rc = take_status_word(&st))) {
+            cudaFree(buf);
+            return rc;
+        }
         cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        cudaMemsetAsync(st, 0, sizeof(int), s);
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         auto trial = [&](const PlanTune &t, double *ms) -> int {
             std::unique_ptr<gf2x_plan> pl(new gf2x_plan());
             int r = plan_init(pl.get(), na_bits, nb_bits, &t);
             if (r) return r;
-            if ((r = plan_run_core(pl.get(), da, db, dout, buf, s, T, device_status(), nullptr)))
+            if ((r = plan_run_core(pl.get(), da, db, dout, buf, s, T, st, nullptr)))
                 return GF2X_ECUDA;
             cudaEventRecord(e0, s);
             for (int i = 0; i < reps; i++)
-                if (plan_run_core(pl.get(), da, db, dout, buf, s, T, device_status(), nullptr))
+                if (plan_run_core(pl.get(), da, db, dout, buf, s, T, st, nullptr))
                     return GF2X_ECUDA;
             cudaEventRecord(e1, s);
             if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -866,12 +996,13 @@ int gf2x_autotune(uint64_t na_bits, uint64_t nb_bits, int reps, gf2x_tune_t *bes
                 }
             }
         cudaStreamSynchronize(s);
+        const int ds = read_clear_status(st);
+        give_status_word(st);
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         cudaStreamDestroy(s);
         cudaFree(buf);
-        const int st = take_device_status();
-        if (rc == GF2X_OK) rc = st;
+        if (rc == GF2X_OK) rc = ds;
         if (rc) return rc;
         tune_store(shape_key(na_bits, nb_bits), bestE);
         *best = to_abi(bestE);
@@ -949,6 +1080,26 @@ int gf2x_tune_load(const char *path) {
     return GF2X_OK;
 }
 
+int gf2x_stream_status(gf2x_stream_t stream) {
+    try {
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return GF2X_ECUDA;
+        }
+        int *st = stream_status_word(s);
+        if (!st) return GF2X_ECUDA;
+        return read_clear_status(st);
+    } catch (...) {
+        return GF2X_ECUDA;
+    }
+}
+
+int gf2x_debug_set_wait_spins(int64_t spins) {
+    set_wait_spins(spins);
+    return GF2X_OK;
+}
+
 int gf2x_shutdown(void) {
     {
         std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -968,6 +1119,8 @@ int gf2x_shutdown(void) {
             cudaSetDevice(kv.first);
             cudaFree(kv.second.status);
             kv.second.status = nullptr;
+            kv.second.free_words.clear();
+            kv.second.stream_words.clear();
         }
         if (kv.second.pool) {
             cudaSetDevice(kv.first);

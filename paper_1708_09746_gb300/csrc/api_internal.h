@@ -11,8 +11,13 @@ namespace api {
 
 // Size-independent device tables of the current device (uploaded on first use).
 int tables(const DevTables **T);
-// Device status word of the current device (valid after tables()).
-int *status_word();
+// Status word of the asynchronous calls on stream s of the current device
+// (gf2x_stream_status reads it); nullptr if the device has no tables.
+int *stream_status(cudaStream_t s);
+// A status word for one caller of its own (a server slot); GF2X_EBUSY when
+// none is free.  give_status returns it once its work has finished.
+int take_status(int **w);
+void give_status(int *w);
 // Cached plan for these operand sizes on the current device.
 int plan_for(uint64_t na_bits, uint64_t nb_bits, std::shared_ptr<gf2x_plan> *p);
 // Argument checks of one product (device pointers, sizes, overlap).

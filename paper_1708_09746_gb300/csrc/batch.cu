@@ -45,6 +45,7 @@ struct gf2x_batch {
     cudaStream_t cap = nullptr;  // private stream for capture
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t done = nullptr;
+    int *st = nullptr;  // the batch's own status word (a library word)
     bool launched = false;
     std::mutex mu;
 };
@@ -111,11 +112,11 @@ void fill_descs(const gf2x_batch *B, const uint64_t *const *a, const uint64_t *c
 
 // Every chunk, one after another, on s (workspace reused).
 int enqueue_chunks(const gf2x_batch *B, const OperandDesc *da, const OperandDesc *db,
-                   const OutputDesc *dout, void *ws, cudaStream_t s, StageHook *hook) {
+                   const OutputDesc *dout, void *ws, cudaStream_t s, StageHook *hook, int *st) {
     const DevTables *T;
     int rc = api::tables(&T);
     if (rc) return rc;
-    int *st = api::status_word();
+    if (!st) return GF2X_ECUDA;
     const OperandDesc none_in{nullptr, 0, 0};
     const OutputDesc none_out{nullptr, 0, 0};
     for (const auto &ch : B->chunks) {
@@ -171,7 +172,7 @@ int gf2x_mul_batched(int count, const uint64_t *const *a, const uint64_t *na_bit
         cudaMemcpyAsync(db, hb.data(), n * sizeof(OperandDesc), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(dout, ho.data(), n * sizeof(OutputDesc), cudaMemcpyHostToDevice, s);
         std::unique_ptr<StageHook> tm(api::new_timer(s));
-        rc = enqueue_chunks(&B, da, db, dout, mem + ws_off, s, tm.get());
+        rc = enqueue_chunks(&B, da, db, dout, mem + ws_off, s, tm.get(), api::stream_status(s));
         api::ws_free(mem, s);
         if (rc == GF2X_OK && cudaGetLastError() != cudaSuccess) rc = GF2X_ECUDA;
         return rc;
@@ -210,6 +211,10 @@ int gf2x_batch_create(int count, const uint64_t *na_bits, const uint64_t *nb_bit
             cudaGetLastError();
             gf2x_batch_destroy(B.release());
             return GF2X_ENOMEM;
+        }
+        if ((rc = api::take_status(&B->st))) {
+            gf2x_batch_destroy(B.release());
+            return rc;
         }
         *out = B.release();
         return GF2X_OK;
@@ -259,11 +264,12 @@ int gf2x_batch_execute(gf2x_batch *B, const uint64_t *const *a, const uint64_t *
                 cudaGetLastError();
                 return GF2X_ECUDA;
             }
+            cudaMemsetAsync(B->st, 0, sizeof(int), B->cap);
             cudaMemcpyAsync(B->d_a, B->h_a, n * sizeof(OperandDesc), cudaMemcpyHostToDevice, B->cap);
             cudaMemcpyAsync(B->d_b, B->h_b, n * sizeof(OperandDesc), cudaMemcpyHostToDevice, B->cap);
             cudaMemcpyAsync(B->d_out, B->h_out, n * sizeof(OutputDesc), cudaMemcpyHostToDevice,
                             B->cap);
-            rc = enqueue_chunks(B, B->d_a, B->d_b, B->d_out, B->ws, B->cap, nullptr);
+            rc = enqueue_chunks(B, B->d_a, B->d_b, B->d_out, B->ws, B->cap, nullptr, B->st);
             cudaError_t e = cudaStreamEndCapture(B->cap, &g);
             if (rc || e != cudaSuccess || !g) {
                 cudaGetLastError();
@@ -302,9 +308,26 @@ int gf2x_batch_destroy(gf2x_batch *B) {
     cudaFreeHost(B->h_a);
     cudaFreeHost(B->h_b);
     cudaFreeHost(B->h_out);
+    api::give_status(B->st);
     cudaGetLastError();
     delete B;
     return GF2X_OK;
+}
+
+int gf2x_batch_status(gf2x_batch *B) {
+    if (!B) return GF2X_EINVAL;
+    std::lock_guard<std::mutex> lk(B->mu);
+    if (!B->launched) return GF2X_OK;
+    if (cudaEventSynchronize(B->done) != cudaSuccess) {
+        cudaGetLastError();
+        return GF2X_ECUDA;
+    }
+    int v = 0;
+    if (cudaMemcpy(&v, B->st, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return GF2X_ECUDA;
+    }
+    return v;
 }
 
 }  // extern "C"

@@ -3,25 +3,36 @@
 // A pass covers the g consecutive layers k_lo .. k_lo+g-1 of the N-point
 // transform.  Its CTA owns a tile of 2^g "rows" (index bits k_lo .. k_lo+g-1)
 // by 2^c "columns" (index bits 0 .. c-1, consecutive elements, so that the
-// tile moves through HBM in 512-byte runs); the remaining index bits name the
-// CTA.  The tile is loaded into shared memory once, all g layers are applied,
-// and it is written back once.
+// tile moves through HBM in runs of at least 512 bytes); the remaining index
+// bits name the tile.  The tile is loaded into shared memory once (bulk
+// copies completed on an mbarrier), all g layers are applied, and it is
+// written back once.  A strided pass has c = 12 - g >= 5 (g <= 7); the bottom
+// pass is contiguous (c = 0) over the layers 0 .. 11 of 4096 elements.
 //
 // Multiplier of a butterfly of layer k = k_lo + r at tile row `row`:
 //   s_k(phi(idx with bits <= k cleared))
 //     = s_k(phi(hi << (k_lo+g)))  XOR  s_k(phi((row >> (r+1)) << (k+1)))
 //     =        cval[r]            XOR       d(k, row >> (r+1))
-// by the linearity of s_k (Sec. 4.4).  cval[r] is the same for the whole CTA;
+// by the linearity of s_k (Sec. 4.4).  cval[r] is the same for the whole tile;
 // d(k, prefix) is the same for every tile and is precomputed per pass.
 //
-// Layers whose butterflies can be laid out so that the 32 lanes of a warp
-// share the multiplier (column bits plus lower rows span >= 5 index bits) are
-// processed four at a time in registers with warp-shuffle tables (the table
-// of cval[r] is built once per CTA, the table of d is precomputed; the table
-// of their sum is the XOR of the two).  The lowest layers of the contiguous
-// bottom pass (k < 5, multiplier changes every 2^(k+1) elements) use the
-// F~_{2^8} product table in shared memory, one layer per sweep.
+// How each row's butterflies multiply (gf2x_mul.cuh):
+//  * rows whose butterflies can be laid out so that the 32 lanes of a warp
+//    share the multiplier (column bits plus lower rows span >= 5 index bits):
+//    whole elements in registers, up to three rows per register sub-pass,
+//    warp-shuffle tables (the table of cval[r] is built once per tile, the
+//    table of d is precomputed; the table of their sum is the XOR of the two);
+//  * rows 3-5 of the bottom pass: one limb-wise sub-pass (a lane holds one
+//    32-bit limb of 8 elements, so a warp's lanes share the multiplier of a
+//    group of up to 64 elements) with the same shuffle tables;
+//  * rows 0-2 of a bottom tile of at least 2^8 elements: one register
+//    sub-pass per lane group of 8 elements; the multiplier's warp-uniform part
+//    through the shuffle tables, its per-lane F~_{2^8} part through a per-lane
+//    byte table;
+//  * lane-varying rows of smaller tiles: the F~_{2^8} product table in shared
+//    memory, one row per sweep.
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -34,6 +45,15 @@
 #include "tma.cuh"
 
 namespace gf2x {
+
+namespace {
+std::atomic<uint32_t> g_wait_spins{kWaitSpins};
+}
+
+void set_wait_spins(int64_t spins) {
+    g_wait_spins.store(spins < 0 ? kWaitSpins : (uint32_t)std::min<int64_t>(spins, 0xffffffffll));
+}
+uint32_t wait_spins() { return g_wait_spins.load(); }
 
 // ---------------------------------------------------------------------------
 // Register sub-pass: G layers (tile rows r_lo .. r_lo+G-1) on columns of 2^G
@@ -398,7 +418,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
                                 &bar[b ^ 1], lane);
                 prefetched = true;
             }
-            ok = mbar_wait_bounded(&bar[b], NB == 2 ? (i >> 1) & 1 : i & 1);
+            ok = mbar_wait_bounded(&bar[b], NB == 2 ? (i >> 1) & 1 : i & 1, a.wait_spins);
         } else {
             if (warp == 0) bulk_wait_read_all();  // the stores out of buf[b] have read it
         }
@@ -494,9 +514,19 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         }
     }
     if (aborted) {
-        if (threadIdx.x == 0) atomicExch(a.status, -4);  // GF2X_ETIMEOUT
-        // let a prefetch already in flight land before the CTA exits
-        if (prefetched && threadIdx.x == 0) mbar_wait_bounded(&bar[(i & 1) ^ 1], ((i + 1) >> 1) & 1);
+        if (threadIdx.x == 0) {
+            atomicExch(a.status, -4);  // GF2X_ETIMEOUT
+            // Let every load still in flight land before the CTA exits (its
+            // shared memory may be handed to another CTA next): the tile whose
+            // wait ran out, and the next tile if it was already prefetched.
+            // These waits take the default bound, not the caller's.
+            if (pipe) {
+                const int b = NB == 2 ? (i & 1) : 0;
+                mbar_wait_bounded(&bar[b], NB == 2 ? (i >> 1) & 1 : i & 1);
+            }
+            if (prefetched) mbar_wait_bounded(&bar[(i & 1) ^ 1], ((i + 1) >> 1) & 1);
+        }
+        __syncthreads();
     }
     cp_async_wait_all();
     if (warp == 0) bulk_wait_all();
@@ -755,6 +785,7 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
     a.strideFA = strideFA == ~0ull ? strideF : strideFA;
     a.strideW = strideW;
     a.nbuf = p.nbuf;
+    a.wait_spins = wait_spins();
     const uint64_t tiles = ((1ull << M) >> (p.g + p.c)) * (uint64_t)count;
     const size_t smem = pass_smem(p.g, p.c, p.uf, p.needs_mt, p.nbuf, p.low3);
     // persistent CTAs: as many as are resident at once; a CTA alone on its SM

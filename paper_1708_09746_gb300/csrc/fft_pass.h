@@ -44,6 +44,7 @@ struct FftPassArgs {
     uint64_t strideF, strideW;  // g64 + y * strideW, FA + y * strideFA
     uint64_t strideFA;          // 0: one transform FA shared by all products
     int nbuf;     // tile buffers (1 or 2)
+    uint32_t wait_spins;  // bound of the tile-load waits (try_wait attempts)
 };
 
 // A fixed-capacity list of passes (no heap allocation).
@@ -95,6 +96,12 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
                     const uint4 *FA, const DevTables *T, int *status, cudaStream_t s,
                     int count = 1, uint64_t strideF = 0, uint64_t strideW = 0,
                     const uint4 *Fsrc = nullptr, uint64_t strideFA = ~0ull);
+
+// Bound of the tile-load waits that launches made from now on use, in
+// try_wait attempts (negative: the default 2^24; 0: every wait gives up at
+// once).  For tests of the timeout path.
+void set_wait_spins(int64_t spins);
+uint32_t wait_spins();
 
 void launch_pointmul_mt(const uint4 *A, const uint4 *B, uint4 *C, uint64_t n, const DevTables *T,
                         cudaStream_t s);

@@ -19,11 +19,13 @@
 //
 // Limits and sharing: products with more than GF2X_NOALLOC_MAX_FFT_POINTS
 // transform points are rejected (GF2X_EINVAL).  All calls share the one
-// scratch array and status word, so calls that overlap on the GPU (other
-// streams, other host threads) race; the call waits for its own stream before
-// it returns.  No part of the scratch needs to start at zero: every kernel
-// writes what it later reads; the status word is cleared on the stream at the
-// start of each call.
+// scratch array and status word.  Work that overlapped on the GPU would race
+// on them, so every call holds a process-wide lock from before its first
+// launch until its stream has drained: calls from other host threads or on
+// other streams wait for it (they never overlap on the GPU), and a thread
+// holding the lock blocks the others until its product is done.  No part of
+// the scratch needs to start at zero: every kernel writes what it later
+// reads; the status word is cleared on the stream at the start of each call.
 #include <mutex>
 
 #include "../../include/gf2x_gb300.h"
@@ -37,11 +39,12 @@ namespace {
 constexpr size_t kScratchBytes = (size_t)GF2X_NOALLOC_SCRATCH_BYTES;
 constexpr int kMaxLog = 18;  // log2 of GF2X_NOALLOC_MAX_FFT_POINTS
 static_assert((1ull << kMaxLog) == GF2X_NOALLOC_MAX_FFT_POINTS, "limit");
-// The workspace of the largest allowed product: two 16-byte arrays of 2^18
-// points, two padded operands of at most 2^17 words and the changeRepr'd
-// blocks of one operand (2^17 elements).
-static_assert(2 * (16ull << kMaxLog) + 2 * (8ull << (kMaxLog - 1)) + (16ull << (kMaxLog - 1)) +
-                      1280 <=
+// The workspace of the largest allowed product: two 16-byte arrays of N =
+// 2^18 points, the padded operands (Pa + Pb <= N + 1 words: the most uneven
+// shape, N words times one word, pads the long operand to N) and the
+// changeRepr'd blocks of the longer one (max(Pa, Pb) <= N elements), plus the
+// 256-byte alignment of five sub-buffers.
+static_assert(2 * (16ull << kMaxLog) + 8 * ((1ull << kMaxLog) + 1) + (16ull << kMaxLog) + 1280 <=
                   kScratchBytes,
               "scratch holds the largest allowed product");
 
@@ -156,7 +159,14 @@ bool is_device_ptr(const void *p) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    // device memory must be the current device's own (the kernels run there)
+    int dev = -1;
+    if (at.type != cudaMemoryTypeDevice || cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.device == dev;
 }
 
 bool overlaps(const void *a, size_t na, const void *b, size_t nb) {

@@ -94,6 +94,8 @@ struct Slot {
     OutputDesc *d_out = nullptr;
     OperandDesc *h_a = nullptr, *h_b = nullptr;  // pinned mirrors
     OutputDesc *h_out = nullptr;
+    int *d_st = nullptr;  // this slot's device status word (a library word)
+    int *h_st = nullptr;  // pinned copy, written at the end of each batch
 };
 
 }  // namespace
@@ -130,7 +132,9 @@ void worker_main(gf2x_server *S) {
             if (!sl.busy) continue;
             cudaError_t q = cudaEventQuery(sl.done);
             if (q == cudaErrorNotReady) continue;
-            const int st = (q == cudaSuccess) ? GF2X_OK : GF2X_ECUDA;
+            // the slot's own status word, copied back before `done`: a bounded
+            // device wait that ran out is reported to this batch's requests
+            const int st = (q == cudaSuccess) ? (*sl.h_st ? *sl.h_st : GF2X_OK) : GF2X_ECUDA;
             if (q != cudaSuccess) cudaGetLastError();
             const auto now = Clock::now();
             for (auto &r : sl.reqs) {
@@ -190,6 +194,8 @@ void worker_main(gf2x_server *S) {
             const DevTables *T;
             rc = api::tables(&T);
             if (!rc) {
+                *sl.h_st = 0;
+                cudaMemsetAsync(sl.d_st, 0, sizeof(int), sl.stream);
                 cudaMemcpyAsync(sl.d_a, sl.h_a, k * sizeof(OperandDesc), cudaMemcpyHostToDevice, sl.stream);
                 cudaMemcpyAsync(sl.d_b, sl.h_b, k * sizeof(OperandDesc), cudaMemcpyHostToDevice, sl.stream);
                 cudaMemcpyAsync(sl.d_out, sl.h_out, k * sizeof(OutputDesc), cudaMemcpyHostToDevice,
@@ -198,9 +204,11 @@ void worker_main(gf2x_server *S) {
                 const OutputDesc none_out{nullptr, 0, 0};
                 rc = plan_run_batch(plan.get(), (int)k, sl.d_a, sl.d_b, sl.d_out, none_in, none_in,
                                     none_out, max_words, S->arena_base + off, plan->ws_bytes,
-                                    sl.stream, T, api::status_word(), nullptr)
+                                    sl.stream, T, sl.d_st, nullptr)
                          ? GF2X_ECUDA
                          : GF2X_OK;
+                if (!rc)
+                    cudaMemcpyAsync(sl.h_st, sl.d_st, sizeof(int), cudaMemcpyDeviceToHost, sl.stream);
             }
             if (!rc && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) rc = GF2X_ECUDA;
             if (rc) {
@@ -255,7 +263,16 @@ int gf2x_server_create(size_t mem_budget_bytes, int max_slots, int max_batch,
                       cudaMalloc(&sl.d_out, kMaxBatch * sizeof(OutputDesc)) == cudaSuccess &&
                       cudaMallocHost(&sl.h_a, kMaxBatch * sizeof(OperandDesc)) == cudaSuccess &&
                       cudaMallocHost(&sl.h_b, kMaxBatch * sizeof(OperandDesc)) == cudaSuccess &&
-                      cudaMallocHost(&sl.h_out, kMaxBatch * sizeof(OutputDesc)) == cudaSuccess;
+                      cudaMallocHost(&sl.h_out, kMaxBatch * sizeof(OutputDesc)) == cudaSuccess &&
+                      cudaMallocHost(&sl.h_st, sizeof(int)) == cudaSuccess;
+            if (ok) {
+                *sl.h_st = 0;
+                rc = api::take_status(&sl.d_st);
+                if (rc) {
+                    gf2x_server_destroy(S.release());
+                    return rc;
+                }
+            }
             if (!ok) {
                 cudaGetLastError();
                 gf2x_server_destroy(S.release());
@@ -382,6 +399,8 @@ int gf2x_server_destroy(gf2x_server *S) {
         cudaFreeHost(sl.h_a);
         cudaFreeHost(sl.h_b);
         cudaFreeHost(sl.h_out);
+        cudaFreeHost(sl.h_st);
+        api::give_status(sl.d_st);
     }
     cudaFree(S->arena_base);
     cudaGetLastError();

@@ -42,9 +42,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Default bound of a wait, in try_wait attempts.
+constexpr uint32_t kWaitSpins = 1u << 24;
+
 // Bounded wait on the phase with the given parity: false if it ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < (1u << 24); i++)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint32_t spins = kWaitSpins) {
+    for (uint32_t i = 0; i < spins; i++)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

@@ -1,8 +1,9 @@
 """Parity at the full workload sizes (2^28 ... 2^33-bit operands), in the
 launch configuration the benchmark times: gf2x_mul_async on a side stream.
 
-A full oracle product at these sizes takes minutes, so the CUDA result is
-checked against (i) product words the oracle computes one by one from the
+The headline 2^28-bit product is compared word for word with the whole
+oracle product.  At the larger sizes a full oracle product takes minutes, so
+the CUDA result is checked against (i) product words the oracle computes one by one from the
 definition c_k = sum_{i+j=k} a_i b_j (word 0, the top words, the words around
 the operands' lengths and seeded random words), (ii) modular fingerprints:
 c mod r = (a mod r)(b mod r) mod r for random irreducible r of degree 64, which
@@ -73,10 +74,24 @@ def _check_sampled(c, a, na, b, nb, seed, n_random=8, n_fp=2):
         assert P.fingerprint_ok(a, na, b, nb, c, r), "fingerprint mod x^64+%#x" % r
 
 
+def test_fullsize_2_28_whole_product_against_oracle():
+    # The headline workload compared word for word with the whole oracle
+    # product (Karatsuba over the host's fastest carry-less word product,
+    # PMULL on an aarch64 host, on all host cores).
+    a, na, b, nb = W.make_workload("c1_2^28")
+    c = _gpu_product(a, na, b, nb)
+    want = P.mul(a, na, b, nb)
+    assert len(c) == len(want)
+    bad = np.flatnonzero(c != want)
+    assert bad.size == 0, "first differing word %d of %d (oracle clmul: %s)" % (
+        int(bad[0]), len(c), P.clmul_kind())
+
+
 @pytest.mark.parametrize("name,n_fp", [
     ("c1_2^28", 4),          # the headline workload
     ("c1_2^29", 2),
     ("c1_2^28_sparse", 2),   # 1 %-dense bits
+    ("c1_2^29_sparse", 2),
     ("c1_2^28x2^16", 4),     # unequal lengths: Pb << N
     ("c2_2^30", 2),
     ("c2_2^32", 1),
@@ -87,10 +102,11 @@ def test_fullsize_sampled(name, n_fp):
     _check_sampled(c, a, na, b, nb, seed=na % 9973 + nb % 997, n_fp=n_fp)
 
 
-def test_fullsize_all_ones_closed_form():
+@pytest.mark.parametrize("name", ["c1_2^28_ones", "c1_2^29_ones"])
+def test_fullsize_all_ones_closed_form(name):
     # (sum_{i<n} x^i)^2 = sum_{i<n} x^(2i) over GF(2): every even bit up to
     # 2n-2, i.e. words 0x5555...; the last word holds the bits below 2n-1.
-    a, na, b, nb = W.make_workload("c1_2^28_ones")
+    a, na, b, nb = W.make_workload(name)
     c = _gpu_product(a, na, b, nb)
     want = np.full(len(c), 0x5555555555555555, dtype=np.uint64)
     rem = (na + nb - 1) % 64

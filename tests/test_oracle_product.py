@@ -45,6 +45,24 @@ def test_clmul64_definition():
             assert lo | (hi << 64) == _ref_int_mul(x, y)
 
 
+def test_clmul64_fast_forms_match_definition():
+    # The 4-bit window form and the form the product routines use (PMULL on
+    # an aarch64 host that has it) against the bit-by-bit definition: every
+    # single-bit pair, structured words, and random pairs.
+    rng = np.random.default_rng(12)
+    vals = [0, 1, 2**64 - 1, 0x5555555555555555, 0xAAAAAAAAAAAAAAAA,
+            0x8000000000000001, 0x0F0F0F0F0F0F0F0F]
+    vals += [1 << i for i in range(64)]
+    pairs = [(x, y) for x in vals for y in vals]
+    r = rng.integers(0, 2**64 - 1, size=(4000, 2), dtype=np.uint64, endpoint=True)
+    pairs += [(int(x), int(y)) for x, y in r]
+    for x, y in pairs:
+        want = P.clmul64(x, y)
+        assert P.clmul64_win4(x, y) == want, (hex(x), hex(y))
+        assert P.clmul64_fast(x, y) == want, (hex(x), hex(y), P.clmul_kind())
+    assert P.clmul_kind() in ("pmull", "win4")
+
+
 def test_exhaustive_8x8_bits():
     # every pair of polynomials with at most 8 bits
     for a in range(256):
