@@ -384,6 +384,41 @@ def measure_sizes(G, torch, W, dev, stream, flush):
     return res
 
 
+def measure_variants(G, torch, dev, stream, flush, da, na, db, nb, out, ref_ms):
+    """The paper's other forms of the product on the headline workload, each
+    through its own C-ABI call (device time, L2 flushed between products,
+    3 timed runs after one untimed), checked word for word against the
+    headline product's output."""
+    import numpy as np
+    ref = out.clone()
+    res = {}
+    forms = [("tower256_w128", G.gf2x_mul_tower256_async,
+              "F~_{2^256} tower field, 128-bit blocks (Sec. 4.3, Table 2 F~_{2^256} row), %d points"
+              % G.gf2x_tower256_fft_points(na, nb))]
+    for name, fn, desc in forms:
+        try:
+            evs = []
+            with torch.cuda.stream(stream):
+                for i in range(4):
+                    flush.zero_()
+                    out.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fn(da, na, db, nb, out, stream)
+                    e1.record(stream)
+                    evs.append((e0, e1))
+            stream.synchronize()
+            G.gf2x_stream_status(stream)
+            ms = [e0.elapsed_time(e1) for e0, e1 in evs[1:]]
+            v = sum(ms) / len(ms)
+            res[name] = {"ms": v, "vs_f2_128_form": v / ref_ms, "form": desc,
+                         "same_product": bool(torch.equal(out, ref))}
+        except Exception as e:  # report, keep the headline line
+            res[name] = {"error": repr(e)}
+    out.copy_(ref)
+    return res
+
+
 def measure_batched(G, torch, W, dev, stream):
     """4096 products, lengths floor(2^U) with U ~ U[12, 22] per side (seed 7);
     operands are slices of one seeded random-word pool (seed 7)."""
@@ -674,6 +709,9 @@ def run_ours(args):
         "wall_s_timed": wall,
     }
     line["config"]["plan"] = tuned
+    if world == 1:
+        line["variants_ms"] = measure_variants(G, torch, dev, stream, flush, da, na, db, nb, out,
+                                               ms_per_product)
     if not args.no_sizes and world == 1:
         line["sizes_ms"] = measure_sizes(G, torch, W, dev, stream, flush)
     if not args.no_systems and world == 1:

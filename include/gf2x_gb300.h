@@ -348,6 +348,49 @@ GF2X_API int gf2x_mul_noalloc(const uint64_t *a, uint64_t na_bits,
                               const uint64_t *b, uint64_t nb_bits,
                               uint64_t *out, gf2x_stream_t stream);
 
+/* ---- The F~_{2^256} form (w = 128) ----------------------------------------
+ * Sec. 4.3 and the F~_{2^256} row of Table 2: the operands are cut into
+ * 128-bit blocks, BasisCvt converts the blocks, changeRepr maps each block
+ * p(z) into F~_{2^256} = F~_{2^128}[x_8]/(x_8^2 + x_8 + v_127) as p(x_8), the
+ * additive FFT runs over N2 = gf2x_tower256_fft_points points of that field
+ * (half as many as the F~_{2^128} form), pointmul multiplies general
+ * F~_{2^256} elements, and changeRepr^-1 plus the recombination of 128-bit
+ * limbs gives the same product c = a * b.  Elements are held as two
+ * F~_{2^128} halves (lo, the x_8 coefficient) in two arrays of N2 entries. */
+
+/* N2: the smallest power of two >= the product's number of 128-bit blocks
+ * ceil(na/128) + ceil(nb/128) - 1 (at least 2); 0 if either size is 0. */
+GF2X_API uint64_t gf2x_tower256_fft_points(uint64_t na_bits, uint64_t nb_bits);
+
+/* c = a * b by the F~_{2^256} form, synchronous on the legacy default stream
+ * (same conventions and result as gf2x_mul; N2 <= 2^27, operands up to 2^33
+ * bits).  The workspace (4 x 16 N2 bytes plus the padded blocks) comes from
+ * the library's stream-ordered pool. */
+GF2X_API int gf2x_mul_tower256(const uint64_t *a, uint64_t na_bits, const uint64_t *b,
+                               uint64_t nb_bits, uint64_t *out);
+
+/* As gf2x_mul_tower256, asynchronous on `stream` (device-side failures are
+ * reported by gf2x_stream_status). */
+GF2X_API int gf2x_mul_tower256_async(const uint64_t *a, uint64_t na_bits, const uint64_t *b,
+                                     uint64_t nb_bits, uint64_t *out, gf2x_stream_t stream);
+
+/* Stage entry points of the F~_{2^256} form (asynchronous on `stream`, device
+ * pointers), for stage-by-stage checks:
+ *  - changeRepr: `blocks` holds P 128-bit blocks (P a power of two, 16 bytes
+ *    each, little-endian); F receives 2 N2 elements of 16 bytes: F[i] and
+ *    F[N2 + i] are the low half and the x_8 coefficient of p_{i mod P}(x_8)
+ *    (N2 >= P a power of two: the fan-out of the FFT layers above log2 P).
+ *  - pointmul: B[i] := A[i] * B[i] for i < N2, elements split as above.
+ *  - changeRepr^-1 + recombination: out receives out_words words of
+ *    sum_j psi(e_j) z^(128 j), e_j = F[j] + x_8 F[N2 + j], bits at positions
+ *    >= total_bits cleared. */
+GF2X_API int gf2x_stage_chrepr256(const void *blocks, uint64_t P, void *F, uint64_t N2,
+                                  gf2x_stream_t stream);
+GF2X_API int gf2x_stage_pointmul256(const void *A, void *B, uint64_t N2, gf2x_stream_t stream);
+GF2X_API int gf2x_stage_ichrepr256_combine(const void *F, uint64_t N2, uint64_t *out,
+                                           uint64_t out_words, uint64_t total_bits,
+                                           gf2x_stream_t stream);
+
 /* ---- Device-side failures ------------------------------------------------*/
 
 /* Waits for `stream` and returns the status of the asynchronous calls made

@@ -25,6 +25,8 @@ __all__ = [
     "gf2x_server_create", "gf2x_server_submit", "gf2x_server_wait", "gf2x_server_stats",
     "gf2x_server_reset_stats", "gf2x_server_destroy", "gf2x_probe_pipes", "LIB_PATH",
     "gf2x_stream_status", "gf2x_batch_status", "gf2x_debug_set_wait_spins",
+    "gf2x_tower256_fft_points", "gf2x_mul_tower256", "gf2x_mul_tower256_async",
+    "gf2x_stage_chrepr256", "gf2x_stage_pointmul256", "gf2x_stage_ichrepr256_combine",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -105,6 +107,12 @@ _SIGS = {
     "gf2x_stream_status": (_int, [_vp]),
     "gf2x_batch_status": (_int, [_vp]),
     "gf2x_debug_set_wait_spins": (_int, [ctypes.c_int64]),
+    "gf2x_tower256_fft_points": (_u64, [_u64, _u64]),
+    "gf2x_mul_tower256": (_int, [_vp, _u64, _vp, _u64, _vp]),
+    "gf2x_mul_tower256_async": (_int, [_vp, _u64, _vp, _u64, _vp, _vp]),
+    "gf2x_stage_chrepr256": (_int, [_vp, _u64, _vp, _u64, _vp]),
+    "gf2x_stage_pointmul256": (_int, [_vp, _vp, _u64, _vp]),
+    "gf2x_stage_ichrepr256_combine": (_int, [_vp, _u64, _vp, _u64, _u64, _vp]),
 }
 
 
@@ -419,3 +427,33 @@ def gf2x_debug_set_wait_spins(spins):
     """Bound of the kernels' device waits for tests of the timeout path
     (0: give up at once; negative: the default)."""
     _check(load().gf2x_debug_set_wait_spins(int(spins)), "gf2x_debug_set_wait_spins")
+
+
+def gf2x_tower256_fft_points(na_bits, nb_bits):
+    return int(load().gf2x_tower256_fft_points(na_bits, nb_bits))
+
+
+def gf2x_mul_tower256(a, na_bits, b, nb_bits, out):
+    """c = a * b by the F~_{2^256} (w = 128) form, synchronous."""
+    _check(load().gf2x_mul_tower256(_ptr(a), na_bits, _ptr(b), nb_bits, _ptr(out)),
+           "gf2x_mul_tower256")
+
+
+def gf2x_mul_tower256_async(a, na_bits, b, nb_bits, out, stream=None):
+    _check(load().gf2x_mul_tower256_async(_ptr(a), na_bits, _ptr(b), nb_bits, _ptr(out),
+                                          _stream(stream)), "gf2x_mul_tower256_async")
+
+
+def gf2x_stage_chrepr256(blocks, P, F, N2, stream=None):
+    _check(load().gf2x_stage_chrepr256(_ptr(blocks), P, _ptr(F), N2, _stream(stream)),
+           "gf2x_stage_chrepr256")
+
+
+def gf2x_stage_pointmul256(A, B, N2, stream=None):
+    _check(load().gf2x_stage_pointmul256(_ptr(A), _ptr(B), N2, _stream(stream)),
+           "gf2x_stage_pointmul256")
+
+
+def gf2x_stage_ichrepr256_combine(F, N2, out, out_words, total_bits, stream=None):
+    _check(load().gf2x_stage_ichrepr256_combine(_ptr(F), N2, _ptr(out), out_words, total_bits,
+                                                _stream(stream)), "gf2x_stage_ichrepr256_combine")

@@ -489,6 +489,7 @@ int tables(const DevTables **T) { return get_tables(T); }
 int *stream_status(cudaStream_t s) { return stream_status_word(s); }
 int take_status(int **w) { return take_status_word(w); }
 void give_status(int *w) { give_status_word(w); }
+int read_status(int *w) { return read_clear_status(w); }
 int plan_for(uint64_t na_bits, uint64_t nb_bits, std::shared_ptr<gf2x_plan> *p) {
     return cached_plan(na_bits, nb_bits, p);
 }

@@ -18,6 +18,8 @@ int *stream_status(cudaStream_t s);
 // none is free.  give_status returns it once its work has finished.
 int take_status(int **w);
 void give_status(int *w);
+// Reads and clears one status word once the work that writes it has finished.
+int read_status(int *w);
 // Cached plan for these operand sizes on the current device.
 int plan_for(uint64_t na_bits, uint64_t nb_bits, std::shared_ptr<gf2x_plan> *p);
 // Argument checks of one product (device pointers, sizes, overlap).

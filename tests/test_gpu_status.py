@@ -97,13 +97,14 @@ def test_batch_timeout_goes_to_its_batch(pair):
     da, db = to_dev(a), to_dev(b)
     ow = len(want)
     s = torch.cuda.Stream()
-    # a batch captured while the waits give up at once keeps that bound in its
-    # graph; it reports the timeout through gf2x_batch_status
-    with _short_waits():
-        bad = G.gf2x_batch_create([NA, NA], [NB, NB], 64 << 20)
+    # a batch captured (at its first execution) while the waits give up at
+    # once keeps that bound in its graph; it reports the timeout through
+    # gf2x_batch_status
+    bad = G.gf2x_batch_create([NA, NA], [NB, NB], 64 << 20)
     try:
         outs = [empty_dev(ow), empty_dev(ow)]
-        G.gf2x_batch_execute(bad, [da, da], [db, db], outs, s)
+        with _short_waits():
+            G.gf2x_batch_execute(bad, [da, da], [db, db], outs, s)
         with pytest.raises(G.GF2XError) as e:
             G.gf2x_batch_status(bad)
         assert e.value.status == G.GF2X_ETIMEOUT
