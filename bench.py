@@ -394,7 +394,11 @@ def measure_variants(G, torch, dev, stream, flush, da, na, db, nb, out, ref_ms):
     res = {}
     forms = [("tower256_w128", G.gf2x_mul_tower256_async,
               "F~_{2^256} tower field, 128-bit blocks (Sec. 4.3, Table 2 F~_{2^256} row), %d points"
-              % G.gf2x_tower256_fft_points(na, nb))]
+              % G.gf2x_tower256_fft_points(na, nb)),
+             ("simple_gf2_128_poly", G.gf2x_mul_simple_async,
+              "GF(2^128) polynomial basis, Cantor-basis points, general products by emulated "
+              "carry-less multiply (Alg. 4, Table 2 simple row), %d points"
+              % G.gf2x_fft_points(na, nb))]
     for name, fn, desc in forms:
         try:
             evs = []

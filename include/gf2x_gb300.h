@@ -391,6 +391,37 @@ GF2X_API int gf2x_stage_ichrepr256_combine(const void *F, uint64_t N2, uint64_t 
                                            uint64_t out_words, uint64_t total_bits,
                                            gf2x_stream_t stream);
 
+/* ---- The simple polynomial-basis form (Alg. 4) ---------------------------
+ * Sec. 3.1: the working field is the polynomial basis of the AES-GCM field
+ * GF(2)[z]/(z^128 + z^7 + z^2 + z + 1), the LCH FFT evaluates at the points
+ * phi_beta(i) of a Cantor basis (beta_0 = 1, beta_i^2 + beta_i = beta_{i-1},
+ * each beta_i the root with coefficient 0 at z^0), the butterfly multipliers
+ * s_k(alpha) = phi_beta(2b) are general field elements, and a 64-bit block is
+ * a field element as it stands (no changeRepr).  Every multiplication is a
+ * general GF(2^128) product (emulated carry-less multiply and reduction); the
+ * form exists to be compared with the tower form, whose butterfly
+ * multipliers lie in a small subfield.  Same result as gf2x_mul. */
+
+/* c = a * b by the simple form, synchronous on the legacy default stream
+ * (same conventions as gf2x_mul; N <= 2^28 points). */
+GF2X_API int gf2x_mul_simple(const uint64_t *a, uint64_t na_bits, const uint64_t *b,
+                             uint64_t nb_bits, uint64_t *out);
+
+/* As gf2x_mul_simple, asynchronous on `stream`. */
+GF2X_API int gf2x_mul_simple_async(const uint64_t *a, uint64_t na_bits, const uint64_t *b,
+                                   uint64_t nb_bits, uint64_t *out, gf2x_stream_t stream);
+
+/* Stage entry points of the simple form (asynchronous, device pointers):
+ *  - FFT_LCH (inverse = 0) or its inverse over GF(2^128) in the polynomial
+ *    basis on 2^log_n elements of 16 bytes (element i = (lo, hi) 64-bit
+ *    words), layers 0 .. layers-1 only (the forward transform of a
+ *    polynomial of 2^layers coefficients whose input already repeats them
+ *    periodically; layers = log_n for the whole transform);
+ *  - the general product B[i] := A[i] * B[i] for i < n. */
+GF2X_API int gf2x_stage_fft_simple(void *F, int log_n, int layers, int inverse,
+                                   gf2x_stream_t stream);
+GF2X_API int gf2x_stage_gfmul_simple(const void *A, void *B, uint64_t n, gf2x_stream_t stream);
+
 /* ---- Device-side failures ------------------------------------------------*/
 
 /* Waits for `stream` and returns the status of the asynchronous calls made

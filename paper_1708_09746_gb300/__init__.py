@@ -27,6 +27,7 @@ __all__ = [
     "gf2x_stream_status", "gf2x_batch_status", "gf2x_debug_set_wait_spins",
     "gf2x_tower256_fft_points", "gf2x_mul_tower256", "gf2x_mul_tower256_async",
     "gf2x_stage_chrepr256", "gf2x_stage_pointmul256", "gf2x_stage_ichrepr256_combine",
+    "gf2x_mul_simple", "gf2x_mul_simple_async", "gf2x_stage_fft_simple", "gf2x_stage_gfmul_simple",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -113,6 +114,10 @@ _SIGS = {
     "gf2x_stage_chrepr256": (_int, [_vp, _u64, _vp, _u64, _vp]),
     "gf2x_stage_pointmul256": (_int, [_vp, _vp, _u64, _vp]),
     "gf2x_stage_ichrepr256_combine": (_int, [_vp, _u64, _vp, _u64, _u64, _vp]),
+    "gf2x_mul_simple": (_int, [_vp, _u64, _vp, _u64, _vp]),
+    "gf2x_mul_simple_async": (_int, [_vp, _u64, _vp, _u64, _vp, _vp]),
+    "gf2x_stage_fft_simple": (_int, [_vp, _int, _int, _int, _vp]),
+    "gf2x_stage_gfmul_simple": (_int, [_vp, _vp, _u64, _vp]),
 }
 
 
@@ -457,3 +462,23 @@ def gf2x_stage_pointmul256(A, B, N2, stream=None):
 def gf2x_stage_ichrepr256_combine(F, N2, out, out_words, total_bits, stream=None):
     _check(load().gf2x_stage_ichrepr256_combine(_ptr(F), N2, _ptr(out), out_words, total_bits,
                                                 _stream(stream)), "gf2x_stage_ichrepr256_combine")
+
+
+def gf2x_mul_simple(a, na_bits, b, nb_bits, out):
+    """c = a * b by the simple polynomial-basis form (Alg. 4), synchronous."""
+    _check(load().gf2x_mul_simple(_ptr(a), na_bits, _ptr(b), nb_bits, _ptr(out)), "gf2x_mul_simple")
+
+
+def gf2x_mul_simple_async(a, na_bits, b, nb_bits, out, stream=None):
+    _check(load().gf2x_mul_simple_async(_ptr(a), na_bits, _ptr(b), nb_bits, _ptr(out),
+                                        _stream(stream)), "gf2x_mul_simple_async")
+
+
+def gf2x_stage_fft_simple(F, log_n, layers, inverse, stream=None):
+    _check(load().gf2x_stage_fft_simple(_ptr(F), int(log_n), int(layers), int(inverse),
+                                        _stream(stream)), "gf2x_stage_fft_simple")
+
+
+def gf2x_stage_gfmul_simple(A, B, n, stream=None):
+    _check(load().gf2x_stage_gfmul_simple(_ptr(A), _ptr(B), n, _stream(stream)),
+           "gf2x_stage_gfmul_simple")
