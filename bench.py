@@ -398,7 +398,11 @@ def measure_variants(G, torch, dev, stream, flush, da, na, db, nb, out, ref_ms):
              ("simple_gf2_128_poly", G.gf2x_mul_simple_async,
               "GF(2^128) polynomial basis, Cantor-basis points, general products by emulated "
               "carry-less multiply (Alg. 4, Table 2 simple row), %d points"
-              % G.gf2x_fft_points(na, nb))]
+              % G.gf2x_fft_points(na, nb)),
+             ("frobenius_truncated", G.gf2x_mul_frobenius_async,
+              "Frobenius partition / truncated additive FFT, GF(2^128) polynomial basis, "
+              "BasisCvt on bits, 7-layer encoding (Appendix C, Table 3), %d points"
+              % (1 << G.gf2x_frobenius_points(na, nb)))]
     for name, fn, desc in forms:
         try:
             evs = []

@@ -422,6 +422,43 @@ GF2X_API int gf2x_stage_fft_simple(void *F, int log_n, int layers, int inverse,
                                    gf2x_stream_t stream);
 GF2X_API int gf2x_stage_gfmul_simple(const void *A, void *B, uint64_t n, gf2x_stream_t stream);
 
+/* ---- The Frobenius-partition form (Appendix C) ---------------------------
+ * No Kronecker segmentation: a polynomial of degree < 128 n (n = 2^m) is
+ * evaluated, its coefficients taken as elements of GF(2^128) (the polynomial
+ * basis of the simple form), at the n points beta_{m+64} + V_m of the Cantor
+ * basis; this map is a bijection onto GF(2^128)^n (Proposition C.1), so
+ * c = a b needs n = 2^m points with 128 n >= na + nb - 1: half as many as the
+ * 64-bit Kronecker forms.  The map is a truncated additive FFT: BasisCvt of
+ * the one-bit coefficients, an "encoding" of the 128 bits at stride n into one
+ * element (the seven truncated layers), and an m-layer FFT whose multipliers
+ * are general field elements.  Same result as gf2x_mul. */
+
+/* m, the log2 of the number of points of the product (-1 if a size is 0). */
+GF2X_API int gf2x_frobenius_points(uint64_t na_bits, uint64_t nb_bits);
+
+/* c = a * b by the Frobenius-partition form, synchronous on the legacy
+ * default stream (same conventions as gf2x_mul; n <= 2^27 points). */
+GF2X_API int gf2x_mul_frobenius(const uint64_t *a, uint64_t na_bits, const uint64_t *b,
+                                uint64_t nb_bits, uint64_t *out);
+
+/* As gf2x_mul_frobenius, asynchronous on `stream`. */
+GF2X_API int gf2x_mul_frobenius_async(const uint64_t *a, uint64_t na_bits, const uint64_t *b,
+                                      uint64_t nb_bits, uint64_t *out, gf2x_stream_t stream);
+
+/* Stage entry points of the Frobenius form (asynchronous, device pointers):
+ *  - BasisCvt (inverse = 0) or iBasisCvt of 2^log_bits one-bit coefficients
+ *    packed little-endian in max(1, 2^(log_bits-6)) words, in place;
+ *  - the encoding (decode = 0): E[i] = sum_j g[i + j 2^m] w_j, i < 2^m, over
+ *    the 2^log_bits bits of g (log_bits <= m + 7); or its inverse (decode = 1):
+ *    the 128 2^m bits of g (written) from the 2^m elements E;
+ *  - FFT_LCH (inverse = 0) or its inverse over the 2^m points
+ *    beta_{m+64} + phi_beta(i), in place on 2^m elements of 16 bytes. */
+GF2X_API int gf2x_stage_bit_basis_cvt(uint64_t *f, int log_bits, int inverse,
+                                      gf2x_stream_t stream);
+GF2X_API int gf2x_stage_frobenius_encode(const uint64_t *g, int log_bits, int m, void *E,
+                                         int decode, gf2x_stream_t stream);
+GF2X_API int gf2x_stage_fft_frobenius(void *F, int m, int inverse, gf2x_stream_t stream);
+
 /* ---- Device-side failures ------------------------------------------------*/
 
 /* Waits for `stream` and returns the status of the asynchronous calls made

@@ -28,6 +28,8 @@ __all__ = [
     "gf2x_tower256_fft_points", "gf2x_mul_tower256", "gf2x_mul_tower256_async",
     "gf2x_stage_chrepr256", "gf2x_stage_pointmul256", "gf2x_stage_ichrepr256_combine",
     "gf2x_mul_simple", "gf2x_mul_simple_async", "gf2x_stage_fft_simple", "gf2x_stage_gfmul_simple",
+    "gf2x_frobenius_points", "gf2x_mul_frobenius", "gf2x_mul_frobenius_async",
+    "gf2x_stage_bit_basis_cvt", "gf2x_stage_frobenius_encode", "gf2x_stage_fft_frobenius",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -118,6 +120,12 @@ _SIGS = {
     "gf2x_mul_simple_async": (_int, [_vp, _u64, _vp, _u64, _vp, _vp]),
     "gf2x_stage_fft_simple": (_int, [_vp, _int, _int, _int, _vp]),
     "gf2x_stage_gfmul_simple": (_int, [_vp, _vp, _u64, _vp]),
+    "gf2x_frobenius_points": (_int, [_u64, _u64]),
+    "gf2x_mul_frobenius": (_int, [_vp, _u64, _vp, _u64, _vp]),
+    "gf2x_mul_frobenius_async": (_int, [_vp, _u64, _vp, _u64, _vp, _vp]),
+    "gf2x_stage_bit_basis_cvt": (_int, [_vp, _int, _int, _vp]),
+    "gf2x_stage_frobenius_encode": (_int, [_vp, _int, _int, _vp, _int, _vp]),
+    "gf2x_stage_fft_frobenius": (_int, [_vp, _int, _int, _vp]),
 }
 
 
@@ -482,3 +490,33 @@ def gf2x_stage_fft_simple(F, log_n, layers, inverse, stream=None):
 def gf2x_stage_gfmul_simple(A, B, n, stream=None):
     _check(load().gf2x_stage_gfmul_simple(_ptr(A), _ptr(B), n, _stream(stream)),
            "gf2x_stage_gfmul_simple")
+
+
+def gf2x_frobenius_points(na_bits, nb_bits):
+    return int(load().gf2x_frobenius_points(na_bits, nb_bits))
+
+
+def gf2x_mul_frobenius(a, na_bits, b, nb_bits, out):
+    """c = a * b by the Frobenius-partition form (Appendix C), synchronous."""
+    _check(load().gf2x_mul_frobenius(_ptr(a), na_bits, _ptr(b), nb_bits, _ptr(out)),
+           "gf2x_mul_frobenius")
+
+
+def gf2x_mul_frobenius_async(a, na_bits, b, nb_bits, out, stream=None):
+    _check(load().gf2x_mul_frobenius_async(_ptr(a), na_bits, _ptr(b), nb_bits, _ptr(out),
+                                           _stream(stream)), "gf2x_mul_frobenius_async")
+
+
+def gf2x_stage_bit_basis_cvt(f, log_bits, inverse, stream=None):
+    _check(load().gf2x_stage_bit_basis_cvt(_ptr(f), int(log_bits), int(inverse), _stream(stream)),
+           "gf2x_stage_bit_basis_cvt")
+
+
+def gf2x_stage_frobenius_encode(g, log_bits, m, E, decode, stream=None):
+    _check(load().gf2x_stage_frobenius_encode(_ptr(g), int(log_bits), int(m), _ptr(E), int(decode),
+                                              _stream(stream)), "gf2x_stage_frobenius_encode")
+
+
+def gf2x_stage_fft_frobenius(F, m, inverse, stream=None):
+    _check(load().gf2x_stage_fft_frobenius(_ptr(F), int(m), int(inverse), _stream(stream)),
+           "gf2x_stage_fft_frobenius")

@@ -2,27 +2,17 @@
 // in the polynomial basis of GF(2^128) = GF(2)[z] / (z^128 + z^7 + z^2 + z + 1)
 // (the AES-GCM field of Sec. 2.3), the LCH FFT evaluates at the points
 // phi_beta(i) of a Cantor basis (beta_i) of that field, and every product --
-// in the butterflies and in pointmul -- is a general GF(2^128) product.
+// in the butterflies and in pointmul -- is a general GF(2^128) product
+// (poly_field.cu: field, Cantor basis, emulated carry-less multiply, FFT
+// passes).
 //
 // * A 64-bit block p(z) is already a field element of degree < 64 and two
 //   blocks multiply to degree <= 126 without reduction, so the block embeds
 //   as itself (no changeRepr) and the interpolated coefficients are the
 //   chunk products themselves (no changeRepr^-1).
-// * The Cantor basis: beta_0 = 1 and beta_i the root of y^2 + y = beta_{i-1}
-//   whose coefficient at z^0 is 0 (the two roots differ by 1).  In a Cantor
-//   basis s_k(phi_beta(j)) = phi_beta(j >> k) (Sec. 2.4), so the multiplier of
-//   layer k for the butterfly block b (points phi_beta(b 2^(k+1)) + V_{k+1})
-//   is phi_beta(2 b), the XOR of beta_i over the set bits of 2 b: Cantor
-//   coordinates switched to the polynomial basis by a linear map (Alg. 4).
 // * BasisCvt and iBasisCvt are the kernels of the tower form: the novelpoly
 //   basis polynomials have coefficients in GF(2) and are the same for every
 //   Cantor basis.
-// * GB300 has no carry-less multiply instruction: a 32x32-bit carry-less
-//   product is four interleaved integer products per output class (operand
-//   bits spaced four apart, so no column sum reaches the next class), 64 and
-//   128 bits follow by Karatsuba, and the 256-bit product is reduced with
-//   z^128 = z^7 + z^2 + z + 1 (two foldings).  This is the general multiply
-//   whose cost the tower field avoids; the two forms are measured side by side.
 #include <algorithm>
 #include <map>
 #include <memory>
@@ -36,197 +26,10 @@
 #include "api_internal.h"
 #include "kernels.h"
 #include "plan.h"
+#include "poly_field.h"
 
 namespace gf2x {
 namespace {
-
-// ---- Host: the field and its Cantor basis ---------------------------------
-
-struct H128 {
-    uint64_t lo, hi;
-};
-
-bool hbit(const H128 &x, int j) { return ((j < 64 ? x.lo : x.hi) >> (j & 63)) & 1; }
-void hflip(H128 &x, int j) { (j < 64 ? x.lo : x.hi) ^= 1ull << (j & 63); }
-
-// Product modulo z^128 + z^7 + z^2 + z + 1, shift-and-add with reduction at
-// every step (z * x = x << 1, plus 0x87 when bit 127 falls out).
-H128 hmul(H128 a, H128 b) {
-    H128 r{0, 0};
-    for (int i = 0; i < 128; i++) {
-        if (hbit(b, i)) {
-            r.lo ^= a.lo;
-            r.hi ^= a.hi;
-        }
-        const bool top = (a.hi >> 63) & 1;
-        a.hi = (a.hi << 1) | (a.lo >> 63);
-        a.lo <<= 1;
-        if (top) a.lo ^= 0x87;
-    }
-    return r;
-}
-
-// y with y^2 + y = c and coefficient 0 at z^0 (the map y -> y^2 + y is
-// GF(2)-linear with kernel {0, 1}): Gauss-Jordan on the columns L(z^j).
-H128 solve_y2_plus_y(H128 c) {
-    H128 col[128];
-    for (int j = 0; j < 128; j++) {
-        H128 e{0, 0};
-        hflip(e, j);
-        col[j] = hmul(e, e);
-        col[j].lo ^= e.lo;
-        col[j].hi ^= e.hi;
-    }
-    // rows[i] = (coefficients of unknown j in equation i, right-hand side)
-    std::vector<H128> rows(128);
-    std::vector<int> rhs(128);
-    for (int i = 0; i < 128; i++) {
-        H128 r{0, 0};
-        for (int j = 0; j < 128; j++)
-            if (hbit(col[j], i)) hflip(r, j);
-        rows[i] = r;
-        rhs[i] = hbit(c, i);
-    }
-    std::vector<int> pivot_row(128, -1);
-    int rank = 0;
-    for (int j = 127; j >= 1; j--) {  // unknown 0 stays free (set to 0)
-        int piv = -1;
-        for (int i = rank; i < 128; i++)
-            if (hbit(rows[i], j)) {
-                piv = i;
-                break;
-            }
-        if (piv < 0) continue;
-        std::swap(rows[rank], rows[piv]);
-        std::swap(rhs[rank], rhs[piv]);
-        for (int i = 0; i < 128; i++)
-            if (i != rank && hbit(rows[i], j)) {
-                rows[i].lo ^= rows[rank].lo;
-                rows[i].hi ^= rows[rank].hi;
-                rhs[i] ^= rhs[rank];
-            }
-        pivot_row[j] = rank++;
-    }
-    // the rows past the rank are zero (column 0 of the map is zero)
-    for (int i = rank; i < 128; i++)
-        if (rhs[i]) throw std::runtime_error("y^2 + y = c has no root");
-    H128 y{0, 0};
-    for (int j = 1; j < 128; j++)
-        if (pivot_row[j] >= 0 && rhs[pivot_row[j]]) hflip(y, j);
-    return y;
-}
-
-// beta_0 .. beta_31 as uint4 (the multipliers use index bits below 32).
-const std::vector<uint4> &cantor_host() {
-    static std::once_flag once;
-    static std::vector<uint4> B;
-    std::call_once(once, [] {
-        H128 b{1, 0};
-        for (int i = 0; i < 32; i++) {
-            if (i) b = solve_y2_plus_y(b);
-            B.push_back(make_uint4((uint32_t)b.lo, (uint32_t)(b.lo >> 32), (uint32_t)b.hi,
-                                   (uint32_t)(b.hi >> 32)));
-        }
-    });
-    return B;
-}
-
-std::mutex g_beta_mu;
-std::map<int, uint4 *> g_beta;
-
-int cantor_dev(const uint4 **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
-        return GF2X_ECUDA;
-    }
-    const std::vector<uint4> &B = cantor_host();
-    std::lock_guard<std::mutex> lk(g_beta_mu);
-    uint4 *&d = g_beta[dev];
-    if (!d) {
-        uint4 *t = nullptr;
-        if (cudaMalloc(&t, B.size() * 16) != cudaSuccess) {
-            cudaGetLastError();
-            return GF2X_ENOMEM;
-        }
-        if (cudaMemcpy(t, B.data(), B.size() * 16, cudaMemcpyHostToDevice) != cudaSuccess) {
-            cudaGetLastError();
-            cudaFree(t);
-            return GF2X_ECUDA;
-        }
-        d = t;
-    }
-    *out = d;
-    return GF2X_OK;
-}
-
-// ---- Device: the general GF(2^128) product ---------------------------------
-
-// 32 x 32 -> 64-bit carry-less product: operand bits split into four classes
-// by position mod 4; the integer product of two classes has its nonzero
-// column sums (at most 8 terms, below 16) in 4-bit fields at the positions of
-// class i + j, so its bit there is the column's parity.  The products of one
-// output class are XORed and masked to that class.
-__device__ __forceinline__ uint64_t clmul32(uint32_t a, uint32_t b) {
-    const uint32_t m = 0x11111111u;
-    const uint32_t a0 = a & m, a1 = a & (m << 1), a2 = a & (m << 2), a3 = a & (m << 3);
-    const uint32_t b0 = b & m, b1 = b & (m << 1), b2 = b & (m << 2), b3 = b & (m << 3);
-    auto mw = [](uint32_t x, uint32_t y) { return (uint64_t)x * (uint64_t)y; };
-    const uint64_t z0 = mw(a0, b0) ^ mw(a1, b3) ^ mw(a2, b2) ^ mw(a3, b1);
-    const uint64_t z1 = mw(a0, b1) ^ mw(a1, b0) ^ mw(a2, b3) ^ mw(a3, b2);
-    const uint64_t z2 = mw(a0, b2) ^ mw(a1, b1) ^ mw(a2, b0) ^ mw(a3, b3);
-    const uint64_t z3 = mw(a0, b3) ^ mw(a1, b2) ^ mw(a2, b1) ^ mw(a3, b0);
-    const uint64_t M = 0x1111111111111111ull;
-    return (z0 & M) | (z1 & (M << 1)) | (z2 & (M << 2)) | (z3 & (M << 3));
-}
-
-// 64 x 64 -> 128 by Karatsuba over 32-bit halves.
-__device__ __forceinline__ void clmul64(uint64_t a, uint64_t b, uint64_t &lo, uint64_t &hi) {
-    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
-    const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
-    const uint64_t p0 = clmul32(a0, b0), p2 = clmul32(a1, b1);
-    const uint64_t pm = clmul32(a0 ^ a1, b0 ^ b1) ^ p0 ^ p2;
-    lo = p0 ^ (pm << 32);
-    hi = p2 ^ (pm >> 32);
-}
-
-// a * b in GF(2)[z]/(z^128 + z^7 + z^2 + z + 1): 128 x 128 by Karatsuba over
-// 64-bit halves, then the high 128 bits H folded twice with z^128 = z^7 + z^2
-// + z + 1 (H (1 + z + z^2 + z^7), whose at most 7 overflowing bits are folded
-// the same way).
-__device__ __forceinline__ uint4 gf128_mul(uint4 a, uint4 b) {
-    const uint64_t A0 = (uint64_t)a.x | ((uint64_t)a.y << 32), A1 = (uint64_t)a.z | ((uint64_t)a.w << 32);
-    const uint64_t B0 = (uint64_t)b.x | ((uint64_t)b.y << 32), B1 = (uint64_t)b.z | ((uint64_t)b.w << 32);
-    uint64_t p0l, p0h, p2l, p2h, pml, pmh;
-    clmul64(A0, B0, p0l, p0h);
-    clmul64(A1, B1, p2l, p2h);
-    clmul64(A0 ^ A1, B0 ^ B1, pml, pmh);
-    pml ^= p0l ^ p2l;
-    pmh ^= p0h ^ p2h;
-    const uint64_t r0 = p0l, r1 = p0h ^ pml, r2 = p2l ^ pmh, r3 = p2h;
-    // H = (r2, r3): H z^128 = H + H z + H z^2 + H z^7
-    const uint64_t t0 = r2 ^ (r2 << 1) ^ (r2 << 2) ^ (r2 << 7);
-    const uint64_t t1 = r3 ^ ((r3 << 1) | (r2 >> 63)) ^ ((r3 << 2) | (r2 >> 62)) ^ ((r3 << 7) | (r2 >> 57));
-    const uint64_t x = (r3 >> 63) ^ (r3 >> 62) ^ (r3 >> 57);
-    const uint64_t u = x ^ (x << 1) ^ (x << 2) ^ (x << 7);
-    const uint64_t lo = r0 ^ t0 ^ u, hi = r1 ^ t1;
-    return make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
-}
-
-__device__ __forceinline__ uint4 xor4s(uint4 a, uint4 b) {
-    return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
-}
-
-// phi_beta(j): XOR of beta_i over the set bits i of j.
-__device__ __forceinline__ uint4 phi_beta(const uint4 *bt, uint32_t j) {
-    uint4 r = make_uint4(0, 0, 0, 0);
-    while (j) {
-        const int i = __ffs(j) - 1;
-        r = xor4s(r, bt[i]);
-        j &= j - 1;
-    }
-    return r;
-}
 
 // ---- Kernels ------------------------------------------------------------------
 
@@ -239,59 +42,6 @@ __global__ void __launch_bounds__(256) k_embed_simple(const uint64_t *__restrict
         const uint64_t v = w[i & (P - 1)];
         F[i] = make_uint4((uint32_t)v, (uint32_t)(v >> 32), 0u, 0u);
     }
-}
-
-// One pass of g layers k_lo .. k_lo+g-1 of FFT_LCH (inverse = 0) or its
-// inverse, on tiles of 2^g rows (index bits k_lo ..) by 2^c consecutive
-// elements, for `count` transforms at F + y * strideF of 2^M points each.
-// The tile is loaded into shared memory, its layers applied one after another
-// (one butterfly per thread per step), and stored back.
-__global__ void __launch_bounds__(256) k_fft_simple(uint4 *F, int M, int k_lo, int g, int c,
-                                                    int inverse, int count, uint64_t strideF,
-                                                    const uint4 *__restrict__ beta) {
-    extern __shared__ __align__(16) uint4 sm[];
-    __shared__ uint4 bt[32];
-    if (threadIdx.x < 32) bt[threadIdx.x] = beta[threadIdx.x];
-    const uint32_t tile = 1u << (g + c), cmask = (1u << c) - 1;
-    const int tiles_log = M - g - c, mid_bits = k_lo - c;
-    const uint64_t ntiles = (uint64_t)count << tiles_log;
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const uint64_t y = t >> tiles_log, tt = t & ((1ull << tiles_log) - 1);
-        const uint64_t base = ((tt >> mid_bits) << (k_lo + g)) | ((tt & ((1ull << mid_bits) - 1)) << c);
-        uint4 *Fy = F + y * strideF;
-        auto gidx = [&](uint32_t q) { return base | ((uint64_t)(q >> c) << k_lo) | (q & cmask); };
-        __syncthreads();  // bt loaded; the previous tile is stored
-        for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) sm[q] = Fy[gidx(q)];
-        __syncthreads();
-        for (int step = 0; step < g; step++) {
-            const int r = inverse ? step : g - 1 - step;
-            const int k = k_lo + r, sh = r + c;
-            for (uint32_t w = threadIdx.x; w < tile / 2; w += blockDim.x) {
-                const uint32_t qu = ((w >> sh) << (sh + 1)) | (w & ((1u << sh) - 1));
-                const uint32_t qv = qu | (1u << sh);
-                const uint4 cm = phi_beta(bt, (uint32_t)(gidx(qu) >> k) & ~1u);
-                uint4 u = sm[qu], v = sm[qv];
-                if (!inverse) {
-                    u = xor4s(u, gf128_mul(cm, v));
-                    v = xor4s(v, u);
-                } else {
-                    v = xor4s(v, u);
-                    u = xor4s(u, gf128_mul(cm, v));
-                }
-                sm[qu] = u;
-                sm[qv] = v;
-            }
-            __syncthreads();
-        }
-        for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) Fy[gidx(q)] = sm[q];
-    }
-}
-
-__global__ void __launch_bounds__(256) k_gfmul_simple(const uint4 *__restrict__ A, uint4 *B,
-                                                      uint64_t n) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        B[i] = gf128_mul(A[i], B[i]);
 }
 
 // The recombination of Sec. 2.1 on the interpolated chunk products (already
@@ -319,40 +69,6 @@ __global__ void __launch_bounds__(256) k_combine_simple(const uint4 *__restrict_
 unsigned grid_simple(uint64_t items, unsigned threads, unsigned per_sm = 8) {
     const uint64_t want = (items + threads - 1) / threads;
     return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)num_sms() * per_sm));
-}
-
-constexpr int kSimpleTileLog = 11;  // 2048 elements, 32 KiB of shared memory
-constexpr int kSimpleDepth = 6;     // layers per strided pass (c = 11 - g >= 5)
-
-// The passes of layers [0, L) of a transform of 2^M points: forward from the
-// top down (strided passes, then the bottom pass), inverse from the bottom up.
-int launch_fft_simple(uint4 *F, int M, int L, int inverse, int count, uint64_t strideF,
-                      const uint4 *beta, cudaStream_t s) {
-    if (L <= 0) return 0;
-    struct P3 {
-        int k_lo, g, c;
-    } ps[8];
-    int n = 0;
-    const int gb = std::min(L, kSimpleTileLog);
-    ps[n++] = P3{0, gb, 0};
-    const int rest = L - gb;
-    if (rest > 0) {
-        const int np = (rest + kSimpleDepth - 1) / kSimpleDepth;
-        int k = gb;
-        for (int i = 0; i < np; i++) {
-            const int g = rest / np + (i < rest % np ? 1 : 0);
-            ps[n++] = P3{k, g, kSimpleTileLog - g};
-            k += g;
-        }
-    }
-    for (int q = 0; q < n; q++) {
-        const P3 &p = inverse ? ps[q] : ps[n - 1 - q];
-        const uint64_t tiles = ((uint64_t)count << (M - p.g - p.c));
-        const size_t smem = (size_t)16 << (p.g + p.c);
-        k_fft_simple<<<(unsigned)std::min<uint64_t>(tiles, (uint64_t)num_sms() * 4), 256, smem, s>>>(
-            F, M, p.k_lo, p.g, p.c, inverse, count, strideF, beta);
-    }
-    return n;
 }
 
 // ---- Plan and stage order -----------------------------------------------------
@@ -394,7 +110,7 @@ int plan_simple_init(PlanSimple *p, uint64_t na_bits, uint64_t nb_bits) {
 int run_simple(const PlanSimple *p, const uint64_t *a, const uint64_t *b, uint64_t *out, void *ws,
                cudaStream_t s, StageHook *hook) {
     const uint4 *beta;
-    int rc = cantor_dev(&beta);
+    int rc = poly::cantor_dev(&beta);
     if (rc) return rc;
     char *base = static_cast<char *>(ws);
     uint4 *FA = reinterpret_cast<uint4 *>(base + p->off_fa);
@@ -424,13 +140,13 @@ int run_simple(const PlanSimple *p, const uint64_t *a, const uint64_t *b, uint64
         k_embed_simple<<<grid_simple(p->N, 256), 256, 0, s>>>(W[x], P[x], F[x], p->N);
         end(1);
         begin(x == 0 ? ST_FFT_A : ST_FFT_B);
-        end(launch_fft_simple(F[x], p->M, lg[x], 0, 1, 0, beta, s));
+        end(poly::launch_fft(F[x], p->M, lg[x], 0, 1, 0, -1, beta, s));
     }
     begin(ST_FUSED);
-    k_gfmul_simple<<<grid_simple(p->N, 256), 256, 0, s>>>(FA, FB, p->N);
+    poly::launch_gfmul(FA, FB, p->N, s);
     end(1);
     begin(ST_IFFT);
-    end(launch_fft_simple(FB, p->M, p->M, 1, 1, 0, beta, s));
+    end(poly::launch_fft(FB, p->M, p->M, 1, 1, 0, -1, beta, s));
     begin(ST_IBCVT);
     end(run_basis_cvt<uint4>(FB, p->M, p->lv_c, 1, s));
     begin(ST_OUT);
@@ -520,10 +236,10 @@ int gf2x_stage_fft_simple(void *F, int log_n, int layers, int inverse, gf2x_stre
     if (log_n < 0 || log_n > kMaxLogN || layers < 0 || layers > log_n) return GF2X_EINVAL;
     try {
         const uint4 *beta;
-        int rc = cantor_dev(&beta);
+        int rc = poly::cantor_dev(&beta);
         if (rc) return rc;
-        launch_fft_simple(static_cast<uint4 *>(F), log_n, layers, inverse ? 1 : 0, 1, 0, beta,
-                          reinterpret_cast<cudaStream_t>(stream));
+        poly::launch_fft(static_cast<uint4 *>(F), log_n, layers, inverse ? 1 : 0, 1, 0, -1, beta,
+                         reinterpret_cast<cudaStream_t>(stream));
         return cudaGetLastError() == cudaSuccess ? GF2X_OK : GF2X_ECUDA;
     } catch (...) {
         return GF2X_ECUDA;
@@ -533,8 +249,8 @@ int gf2x_stage_fft_simple(void *F, int log_n, int layers, int inverse, gf2x_stre
 int gf2x_stage_gfmul_simple(const void *A, void *B, uint64_t n, gf2x_stream_t stream) {
     if (!n) return GF2X_OK;
     try {
-        k_gfmul_simple<<<grid_simple(n, 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-            static_cast<const uint4 *>(A), static_cast<uint4 *>(B), n);
+        poly::launch_gfmul(static_cast<const uint4 *>(A), static_cast<uint4 *>(B), n,
+                           reinterpret_cast<cudaStream_t>(stream));
         return cudaGetLastError() == cudaSuccess ? GF2X_OK : GF2X_ECUDA;
     } catch (...) {
         return GF2X_ECUDA;
