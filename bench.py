@@ -352,18 +352,28 @@ def measure_sizes(G, torch, W, dev, stream, flush):
     products) for the larger single-product workloads."""
     import numpy as np
     res = {}
-    for name in ("c1_2^29", "c1_2^28x2^16", "c2_2^30", "c2_2^32"):
+    for name in ("c1_2^29", "c1_2^28x2^16", "c1_2^28+64", "c1_2^28x64", "c2_2^30", "c2_2^32"):
         a, na, b, nb = W.make_workload(name)
         da = torch.from_numpy(a.view(np.int64)).to(dev)
         db = torch.from_numpy(b.view(np.int64)).to(dev)
         del a, b
         out = torch.empty(G.gf2x_out_words(na, nb), dtype=torch.int64, device=dev)
         # unbalanced operands run by chunks of the long one (their own plan,
-        # default parameters); the others with the shape's autotuned plan
-        chunking = G.gf2x_chunking(na, nb)
-        tuned = ("chunked product (%d chunks of %d words, %d-point transforms), default plan "
-                 "parameters" % (chunking[1], chunking[0], chunking[2])
-                 if chunking[1] else G.gf2x_autotune(na, nb, 2))
+        # default parameters), a short operand directly, a length just past a
+        # power of two by the tail split; the others with the shape's
+        # autotuned plan
+        path, ma, mb = G.gf2x_product_path(na, nb)
+        if path == 1:
+            chunking = G.gf2x_chunking(na, nb)
+            tuned = ("chunked product (%d chunks of %d words, %d-point transforms), default plan "
+                     "parameters" % (chunking[1], chunking[0], chunking[2]))
+        elif path == 2:
+            tuned = "direct product by the short operand (no transform)"
+        elif path == 3:
+            tuned = ("tail split: main product of %d x %d words (%d-point transform) plus the "
+                     "direct tail products" % (ma, mb, G.gf2x_fft_points(64 * ma, 64 * mb)))
+        else:
+            tuned = G.gf2x_autotune(na, nb, 2)
         evs = []
         with torch.cuda.stream(stream):
             for i in range(4):

@@ -90,6 +90,20 @@ GF2X_API uint64_t gf2x_fft_points(uint64_t na_bits, uint64_t nb_bits);
 GF2X_API int gf2x_chunking(uint64_t na_bits, uint64_t nb_bits, uint64_t *chunk_words,
                            uint64_t *chunks, uint64_t *chunk_fft_points);
 
+/* How gf2x_mul / gf2x_mul_async compute a product (host-only, no GPU
+ * needed): *path = 0 one transform of gf2x_fft_points points; 1 by chunks of
+ * the longer operand (gf2x_chunking); 2 directly, without a transform, when
+ * the shorter operand has at most 16 words (each product word is a sum of
+ * 64 x 64 carry-less word products); 3 by the tail split: when cutting at
+ * most 16 words off the operands halves the transform (a word count just
+ * above a power of two), the main product of the first *main_a_words and
+ * *main_b_words words takes the half-length transform and the products of
+ * the cut-off tails by the other operand are added directly
+ * (a b = a0 b0 + x^(64 A) a1 b + x^(64 B) a0 b1).  GF2X_EINVAL for a null
+ * pointer. */
+GF2X_API int gf2x_product_path(uint64_t na_bits, uint64_t nb_bits, int *path,
+                               uint64_t *main_a_words, uint64_t *main_b_words);
+
 /* ---- One-shot products ---------------------------------------------------*/
 
 /* c = a * b (Alg. 5).  Synchronous: enqueues on the legacy default stream,
@@ -98,9 +112,11 @@ GF2X_API int gf2x_chunking(uint64_t na_bits, uint64_t nb_bits, uint64_t *chunk_w
  * shorter's word count rounded up to a power of two, at least 512) are
  * multiplied by chunks: every chunk of the longer operand times one transform
  * of the shorter (transforms of about 2L points), the chunk products XORed
- * into the output at their offsets (distributivity; the same c).  gf2x_mul
- * and gf2x_mul_async do this; plans, batches, the server and the host-buffer
- * call use one transform of the whole product. */
+ * into the output at their offsets (distributivity; the same c).  A shorter
+ * operand of at most 16 words is multiplied directly, and a product just
+ * above a power-of-two length by the tail split (gf2x_product_path).
+ * gf2x_mul and gf2x_mul_async do this; plans, batches, the server and the
+ * host-buffer call use one transform of the whole product. */
 GF2X_API int gf2x_mul(const uint64_t *a, uint64_t na_bits, const uint64_t *b,
              uint64_t nb_bits, uint64_t *out);
 

@@ -30,6 +30,7 @@ __all__ = [
     "gf2x_mul_simple", "gf2x_mul_simple_async", "gf2x_stage_fft_simple", "gf2x_stage_gfmul_simple",
     "gf2x_frobenius_points", "gf2x_mul_frobenius", "gf2x_mul_frobenius_async",
     "gf2x_stage_bit_basis_cvt", "gf2x_stage_frobenius_encode", "gf2x_stage_fft_frobenius",
+    "gf2x_product_path",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -126,6 +127,8 @@ _SIGS = {
     "gf2x_stage_bit_basis_cvt": (_int, [_vp, _int, _int, _vp]),
     "gf2x_stage_frobenius_encode": (_int, [_vp, _int, _int, _vp, _int, _vp]),
     "gf2x_stage_fft_frobenius": (_int, [_vp, _int, _int, _vp]),
+    "gf2x_product_path": (_int, [_u64, _u64, ctypes.POINTER(_int), ctypes.POINTER(_u64),
+                                 ctypes.POINTER(_u64)]),
 }
 
 
@@ -520,3 +523,12 @@ def gf2x_stage_frobenius_encode(g, log_bits, m, E, decode, stream=None):
 def gf2x_stage_fft_frobenius(F, m, inverse, stream=None):
     _check(load().gf2x_stage_fft_frobenius(_ptr(F), int(m), int(inverse), _stream(stream)),
            "gf2x_stage_fft_frobenius")
+
+
+def gf2x_product_path(na_bits, nb_bits):
+    """(path, main_a_words, main_b_words) of the one-shot calls: path 0 one
+    transform, 1 chunks, 2 direct (short operand), 3 tail split."""
+    p, A, B = _int(), _u64(), _u64()
+    _check(load().gf2x_product_path(na_bits, nb_bits, ctypes.byref(p), ctypes.byref(A), ctypes.byref(B)),
+           "gf2x_product_path")
+    return int(p.value), int(A.value), int(B.value)

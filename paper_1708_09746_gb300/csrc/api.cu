@@ -17,6 +17,7 @@
 #include "kernels.h"
 #include "api_internal.h"
 #include "plan.h"
+#include "small.h"
 
 using namespace gf2x;
 
@@ -462,13 +463,62 @@ int mul_chunked(const uint64_t *x, uint64_t x_bits, const uint64_t *y, uint64_t 
     return check_launch();
 }
 
+// A product just above a power-of-two word count: a0 b0 with half the
+// transform, plus the tail products by the direct kernel (small.cu).
+int mul_tails(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64_t nb_bits,
+              uint64_t *out, uint64_t A, uint64_t B, cudaStream_t s, int *st) {
+    const uint64_t aw = words_of(na_bits), bw = words_of(nb_bits);
+    const uint64_t a0_bits = A < aw ? 64 * A : na_bits, b0_bits = B < bw ? 64 * B : nb_bits;
+    const uint64_t ow = gf2x_out_words(na_bits, nb_bits), mw = gf2x_out_words(a0_bits, b0_bits);
+    std::shared_ptr<gf2x_plan> p;
+    int rc = cached_plan(a0_bits, b0_bits, &p);
+    if (rc) return rc;
+    void *ws = nullptr;
+    if ((rc = ws_alloc(&ws, p->ws_bytes, s))) return rc;
+    rc = plan_run(p.get(), a, b, out, ws, s, st);
+    ws_free(ws, s);
+    if (rc) return rc;
+    if (ow > mw && cudaMemsetAsync(out + mw, 0, 8 * (ow - mw), s) != cudaSuccess) {
+        cudaGetLastError();
+        return GF2X_ECUDA;
+    }
+    // a1 b at word A, a0 b1 at word B
+    if (A < aw) launch_mul_small(b, nb_bits, a + A, na_bits - 64 * A, out, ow, A, true, s);
+    if (B < bw) launch_mul_small(a, a0_bits, b + B, nb_bits - 64 * B, out, ow, B, true, s);
+    return check_launch();
+}
+
+// Which way the one-shot calls compute a product: 0 one transform, 1 chunks
+// of the longer operand, 2 direct (a short operand), 3 tail split.
+int product_path(uint64_t na_bits, uint64_t nb_bits, ChunkShape *cs, uint64_t *A, uint64_t *B) {
+    const uint64_t aw = words_of(na_bits), bw = words_of(nb_bits);
+    if (std::min(aw, bw) <= (uint64_t)kSmallWords) return 2;
+    if (chunk_shape(aw, bw, cs) || chunk_shape(bw, aw, cs)) return 1;
+    if (tail_split(aw, bw, A, B)) return 3;
+    return 0;
+}
+
 int mul_on_stream(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64_t nb_bits,
                   uint64_t *out, cudaStream_t s, int *st) {
+    {
+        const uint64_t aw = words_of(na_bits), bw = words_of(nb_bits);
+        if (std::min(aw, bw) <= (uint64_t)kSmallWords) {
+            const uint64_t ow = gf2x_out_words(na_bits, nb_bits);
+            if (bw <= aw)
+                launch_mul_small(a, na_bits, b, nb_bits, out, ow, 0, false, s);
+            else
+                launch_mul_small(b, nb_bits, a, na_bits, out, ow, 0, false, s);
+            return check_launch();
+        }
+    }
     ChunkShape cs;
     if (chunk_shape(words_of(na_bits), words_of(nb_bits), &cs))
         return mul_chunked(a, na_bits, b, nb_bits, out, cs, s, st);
     if (chunk_shape(words_of(nb_bits), words_of(na_bits), &cs))
         return mul_chunked(b, nb_bits, a, na_bits, out, cs, s, st);
+    uint64_t A = 0, B = 0;
+    if (tail_split(words_of(na_bits), words_of(nb_bits), &A, &B))
+        return mul_tails(a, na_bits, b, nb_bits, out, A, B, s, st);
     std::shared_ptr<gf2x_plan> p;
     int rc = cached_plan(na_bits, nb_bits, &p);
     if (rc) return rc;
@@ -538,6 +588,7 @@ int gf2x_chunking(uint64_t na_bits, uint64_t nb_bits, uint64_t *chunk_words, uin
     *chunk_words = *chunks = *chunk_fft_points = 0;
     if (!na_bits || !nb_bits) return GF2X_OK;
     const uint64_t na_w = words_of(na_bits), nb_w = words_of(nb_bits);
+    if (std::min(na_w, nb_w) <= (uint64_t)kSmallWords) return GF2X_OK;  // direct product
     ChunkShape cs;
     uint64_t yw;
     if (chunk_shape(na_w, nb_w, &cs))
@@ -549,6 +600,23 @@ int gf2x_chunking(uint64_t na_bits, uint64_t nb_bits, uint64_t *chunk_words, uin
     *chunk_words = cs.L;
     *chunks = cs.C;
     *chunk_fft_points = 1ull << log2_ceil(std::max<uint64_t>(2, yw + cs.L - 1));
+    return GF2X_OK;
+}
+
+int gf2x_product_path(uint64_t na_bits, uint64_t nb_bits, int *path, uint64_t *main_a_words,
+                      uint64_t *main_b_words) {
+    if (!path || !main_a_words || !main_b_words) return GF2X_EINVAL;
+    *path = 0;
+    *main_a_words = words_of(na_bits);
+    *main_b_words = words_of(nb_bits);
+    if (!na_bits || !nb_bits) return GF2X_OK;
+    ChunkShape cs;
+    uint64_t A = 0, B = 0;
+    *path = product_path(na_bits, nb_bits, &cs, &A, &B);
+    if (*path == 3) {
+        *main_a_words = A;
+        *main_b_words = B;
+    }
     return GF2X_OK;
 }
 

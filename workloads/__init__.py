@@ -156,6 +156,8 @@ WORKLOADS = {
     "c1_2^29_ones": dict(na_bits=1 << 29, nb_bits=1 << 29, seed=None, kind="ones"),
     "c1_2^29_sparse": dict(na_bits=1 << 29, nb_bits=1 << 29, seed=3, kind="sparse"),
     "c1_2^28x2^16": dict(na_bits=1 << 28, nb_bits=1 << 16, seed=4, kind="uniform"),
+    "c1_2^28+64": dict(na_bits=(1 << 28) + 64, nb_bits=(1 << 28) + 64, seed=12, kind="uniform"),
+    "c1_2^28x64": dict(na_bits=1 << 28, nb_bits=64, seed=13, kind="uniform"),
     "c2_2^30": dict(na_bits=1 << 30, nb_bits=1 << 30, seed=5, kind="uniform"),
     "c2_2^32": dict(na_bits=1 << 32, nb_bits=1 << 32, seed=6, kind="uniform"),
 }
