@@ -64,9 +64,26 @@ def test_chunking_host_helper(lib):
     # the c1 unequal workload: chunks of 2^10 words, 2^11-point transforms
     assert G.gf2x_chunking(1 << 28, 1 << 16) == (1024, 4096, 2048)
     assert G.gf2x_chunking(1 << 16, 1 << 28) == (1024, 4096, 2048)
-    # short operand below 512 words: chunks of 512 words
-    assert G.gf2x_chunking(64 * 5000 + 3, 1) == (512, 10, 512)
+    # short operand between 17 and 511 words: chunks of 512 words
+    assert G.gf2x_chunking(64 * 5000 + 3, 64 * 20) == (512, 10, 1024)
     # at most 2^15 chunks: the chunk grows with the long operand
-    L, C, N = G.gf2x_chunking(1 << 33, 64)
-    assert C <= 1 << 15 and L * C >= (1 << 33) // 64 and L == 1 << 12 and N == 1 << 12
+    L, C, N = G.gf2x_chunking(1 << 33, 64 * 17)
+    assert C <= 1 << 15 and L * C >= (1 << 33) // 64 and L == 1 << 12 and N == 1 << 13
     assert G.gf2x_chunking(0, 5) == (0, 0, 0)
+    # a short operand of at most 16 words is multiplied directly (no chunks)
+    assert G.gf2x_chunking(64 * 5000 + 3, 1) == (0, 0, 0)
+    assert G.gf2x_chunking(1 << 33, 64 * 16) == (0, 0, 0)
+
+
+def test_product_path_host_helper(lib):
+    assert G.gf2x_product_path(1 << 28, 1 << 28) == (0, 1 << 22, 1 << 22)
+    assert G.gf2x_product_path(1 << 28, 1 << 16)[0] == 1
+    assert G.gf2x_product_path(1 << 28, 64 * 16)[0] == 2
+    assert G.gf2x_product_path(64 * 16, 1 << 28)[0] == 2
+    assert G.gf2x_product_path(64 * 17, 64 * 17)[0] == 0
+    # one word past half the transform: the main product keeps 2^22 + 2^22
+    # words (a half-length transform), one word of a is a tail
+    assert G.gf2x_product_path((1 << 28) + 64, (1 << 28) + 64) == (3, 1 << 22, (1 << 22) + 1)
+    # 17 words past: no split
+    n = 64 * ((1 << 14) + 9)
+    assert G.gf2x_product_path(n, n)[0] == 0
