@@ -56,7 +56,7 @@ def _args():
                    help="skip the ms-per-product line for 2^29, 2^30 and 2^32 bits")
     p.add_argument("--no-systems", action="store_true",
                    help="skip the batched and serving measurements")
-    p.add_argument("--serve-seconds", type=float, default=3.0)
+    p.add_argument("--serve-seconds", type=float, default=10.0)
     p.add_argument("--cpu-depth", type=int, default=6,
                    help="Karatsuba depth of the CPU-baseline sample (3^d sub-products)")
     return p.parse_args()
@@ -481,18 +481,28 @@ def measure_batched(G, torch, W, dev, stream):
         finally:
             G.gf2x_batch_destroy(batch)
     t_default = run_batch()
-    # autotune every transform shape of the batch, then build the batch again
-    def lg(x):
-        return max(0, (int(x) - 1).bit_length())
-    shapes = {}
-    for x, y in zip(na, nb):
-        wa, wb = (x + 63) // 64, (y + 63) // 64
-        shapes.setdefault((lg(max(2, wa + wb - 1)), lg(wa), lg(wb)), (x, y))
-    t0 = time.perf_counter()
-    for x, y in shapes.values():
-        G.gf2x_autotune(x, y, 2)
-    t_tune = time.perf_counter() - t0
-    t_batch = run_batch()
+    # tune the batch in batch context (each shape group on its own grouped
+    # launch), then replay it
+    batch = G.gf2x_batch_create(na, nb, 8 << 30)
+    try:
+        G.gf2x_batch_execute(batch, A, B, outs, stream)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        groups_before, groups_after = G.gf2x_batch_tune(batch, 2)
+        t_tune = time.perf_counter() - t0
+        G.gf2x_batch_execute(batch, A, B, outs, stream)  # captures the tuned graph
+        stream.synchronize()
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            G.gf2x_batch_execute(batch, A, B, outs, stream)
+        e1.record(stream)
+        stream.synchronize()
+        G.gf2x_batch_status(batch)
+        t_batch = e0.elapsed_time(e1) / 1e3 / reps
+    finally:
+        G.gf2x_batch_destroy(batch)
+    shapes = {"groups_ms_before": groups_before, "groups_ms_after": groups_after}
     del pool, A, B, outs
     torch.cuda.empty_cache()
     return {"workload": "4096 products, per-side lengths log-uniform in [2^12, 2^22] bits, "
@@ -501,9 +511,10 @@ def measure_batched(G, torch, W, dev, stream):
             "batched_default_params_products_per_s": 4096 / t_default,
             "one_by_one_products_per_s": 4096 / t_loop,
             "speedup": t_loop / t_batch, "unit": "products/s",
-            "autotune": {"shapes": len(shapes), "seconds": t_tune},
-            "method": "gf2x_batch_execute (shape-grouped launches, CUDA graph replay) with "
-                      "autotuned per-shape plans vs gf2x_mul_async in a loop, device-timed"}
+            "batch_tune": dict(shapes, seconds=t_tune),
+            "method": "gf2x_batch_execute (shape-grouped launches, direct products by short "
+                      "operands in one launch, CUDA graph replay) tuned in batch context "
+                      "(gf2x_batch_tune) vs gf2x_mul_async in a loop, device-timed"}
 
 
 def measure_serving(G, torch, W, dev, seconds):
@@ -526,7 +537,7 @@ def measure_serving(G, torch, W, dev, seconds):
     pool_words = 1 << 21  # 16 MiB: operands start at seeded offsets in it
     pool = torch.from_numpy(W.random_words(10, 2 * pool_words).view("int64")).to(dev)
     starts = [int(x) % pool_words for x in W.random_words(11, 2 * n)]
-    ring = 256
+    ring = 512  # one output buffer per request in flight
     max_out = (1 << 21) + 2
     outs = torch.empty((ring, max_out), dtype=torch.int64, device=dev)
     res = {}
@@ -552,10 +563,43 @@ def measure_serving(G, torch, W, dev, seconds):
                           "max_batch": batch}
         finally:
             G.gf2x_server_destroy(sv)
+    # saturated: a closed loop keeping `depth` requests in flight (the same
+    # request sequence, cycled) for the same duration: the completed requests
+    # per second show what each server can carry, not the offered load
+    depth = 512
+    sat = {}
+    for label, slots, batch in (("continuous_batching", 8, 64), ("one_at_a_time", 1, 1)):
+        sv = G.gf2x_server_create(16 << 30, slots, batch)
+        try:
+            tickets = []
+            t0 = time.perf_counter()
+            i = 0
+            while time.perf_counter() - t0 < seconds:
+                if len(tickets) >= depth:
+                    G.gf2x_server_wait(sv, tickets[i - depth], 120_000_000)
+                k = i % n
+                a = pool[starts[2 * k]:starts[2 * k] + (na[k] + 63) // 64]
+                b = pool[starts[2 * k + 1]:starts[2 * k + 1] + (nb[k] + 63) // 64]
+                tickets.append(G.gf2x_server_submit(sv, a, na[k], b, nb[k], outs[i % ring]))
+                i += 1
+            for t in tickets[max(0, len(tickets) - depth):]:
+                G.gf2x_server_wait(sv, t, 120_000_000)
+            wall = time.perf_counter() - t0
+            p50, p99, thr, done = G.gf2x_server_stats(sv)
+            sat[label] = {"requests": i, "wall_s": wall, "throughput_per_s": i / wall,
+                          "p50_ms": p50, "p99_ms": p99, "slots": slots, "max_batch": batch}
+        finally:
+            G.gf2x_server_destroy(sv)
+    sat["in_flight"] = depth
+    sat["throughput_ratio"] = (sat["continuous_batching"]["throughput_per_s"] /
+                               sat["one_at_a_time"]["throughput_per_s"])
+    res["saturated"] = sat
     del pool, outs
     torch.cuda.empty_cache()
     res["workload"] = ("Poisson 2000 req/s for %.1f s (%d requests), per-side lengths "
-                       "log-uniform in [2^10, 2^26] bits, 10%% 2^24 x 2^12, seed 8" % (seconds, n))
+                       "log-uniform in [2^10, 2^26] bits, 10%% 2^24 x 2^12, seed 8; saturated: "
+                       "the same requests cycled with %d in flight for %.1f s"
+                       % (seconds, n, depth, seconds))
     res["requests"] = n
     return res
 

@@ -231,6 +231,18 @@ GF2X_API int gf2x_batch_execute(gf2x_batch *batch, const uint64_t *const *a,
                                 gf2x_stream_t stream);
 GF2X_API int gf2x_batch_destroy(gf2x_batch *batch);
 
+/* Tunes the batch in batch context: for every group of products that share a
+ * transform shape, times the group's own grouped launch with candidate plan
+ * parameters (FFT fusion depth and tile buffering, then the BasisCvt tile
+ * shape; the same candidates as gf2x_autotune) and keeps the fastest for that
+ * group of this batch only (the process-wide table of gf2x_autotune is not
+ * changed).  It runs on the operands and outputs of the batch's last
+ * execution, which must still be valid (the outputs are rewritten with the
+ * same values); GF2X_EINVAL if the batch was never executed.  *ms_before and
+ * *ms_after receive the summed device time of the groups with the previous
+ * and the chosen parameters.  The next execution captures the graph again. */
+GF2X_API int gf2x_batch_tune(gf2x_batch *batch, int reps, double *ms_before, double *ms_after);
+
 /* Waits for the batch's last execution and returns GF2X_ETIMEOUT if a bounded
  * device wait in it ran out (its outputs are then undefined), else GF2X_OK
  * (GF2X_OK too if it was never executed). */

@@ -30,7 +30,7 @@ __all__ = [
     "gf2x_mul_simple", "gf2x_mul_simple_async", "gf2x_stage_fft_simple", "gf2x_stage_gfmul_simple",
     "gf2x_frobenius_points", "gf2x_mul_frobenius", "gf2x_mul_frobenius_async",
     "gf2x_stage_bit_basis_cvt", "gf2x_stage_frobenius_encode", "gf2x_stage_fft_frobenius",
-    "gf2x_product_path",
+    "gf2x_product_path", "gf2x_batch_tune",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -129,6 +129,8 @@ _SIGS = {
     "gf2x_stage_fft_frobenius": (_int, [_vp, _int, _int, _vp]),
     "gf2x_product_path": (_int, [_u64, _u64, ctypes.POINTER(_int), ctypes.POINTER(_u64),
                                  ctypes.POINTER(_u64)]),
+    "gf2x_batch_tune": (_int, [_vp, _int, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -532,3 +534,11 @@ def gf2x_product_path(na_bits, nb_bits):
     _check(load().gf2x_product_path(na_bits, nb_bits, ctypes.byref(p), ctypes.byref(A), ctypes.byref(B)),
            "gf2x_product_path")
     return int(p.value), int(A.value), int(B.value)
+
+
+def gf2x_batch_tune(batch, reps=2):
+    """Tunes each shape group of the batch on its own grouped launch (after one
+    execution); returns (ms_before, ms_after) summed over the groups."""
+    b, a = ctypes.c_double(), ctypes.c_double()
+    _check(load().gf2x_batch_tune(batch, int(reps), ctypes.byref(b), ctypes.byref(a)), "gf2x_batch_tune")
+    return float(b.value), float(a.value)

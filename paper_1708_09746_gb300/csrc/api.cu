@@ -550,6 +550,14 @@ int check_product_args(const uint64_t *a, uint64_t na_bits, const uint64_t *b, u
 StageHook *new_timer(cudaStream_t s) { return new StageTimer(s); }
 int ws_alloc(void **p, size_t bytes, cudaStream_t s) { return ::ws_alloc(p, bytes, s); }
 void ws_free(void *p, cudaStream_t s) { ::ws_free(p, s); }
+int make_plan(uint64_t na_bits, uint64_t nb_bits, const PlanTune &t,
+              std::shared_ptr<gf2x_plan> *out) {
+    auto p = std::make_shared<gf2x_plan>();
+    int rc = ::plan_init(p.get(), na_bits, nb_bits, &t);
+    if (rc) return rc;
+    *out = p;
+    return GF2X_OK;
+}
 int run_one(const gf2x_plan *p, const uint64_t *a, const uint64_t *b, uint64_t *out, void *ws,
             cudaStream_t s) {
     return plan_run(p, a, b, out, ws, s, stream_status_word(s));

@@ -20,6 +20,9 @@ int take_status(int **w);
 void give_status(int *w);
 // Reads and clears one status word once the work that writes it has finished.
 int read_status(int *w);
+// A new (uncached) plan for these sizes with the given parameters.
+int make_plan(uint64_t na_bits, uint64_t nb_bits, const PlanTune &t,
+              std::shared_ptr<gf2x_plan> *out);
 // Cached plan for these operand sizes on the current device.
 int plan_for(uint64_t na_bits, uint64_t nb_bits, std::shared_ptr<gf2x_plan> *p);
 // Argument checks of one product (device pointers, sizes, overlap).

@@ -23,12 +23,13 @@
 #include "api_internal.h"
 #include "kernels.h"
 #include "plan.h"
+#include "small.h"
 
 using namespace gf2x;
 
 struct gf2x_batch {
     struct Chunk {
-        std::shared_ptr<gf2x_plan> plan;
+        std::shared_ptr<gf2x_plan> plan;  // null: direct products (short operand)
         int first, count;  // range in the grouped order
         uint64_t max_out_words;
     };
@@ -57,12 +58,18 @@ int batch_build(gf2x_batch *B, int count, const uint64_t *na_bits, const uint64_
     B->count = count;
     B->na.assign(na_bits, na_bits + count);
     B->nb.assign(nb_bits, nb_bits + count);
-    // group by transform shape
+    // group by transform shape; products with a short operand (at most
+    // kSmallWords words) go to one launch of direct products
     std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+    std::vector<int> direct;
     for (int i = 0; i < count; i++) {
         if (!na_bits[i] || !nb_bits[i]) continue;
         if (na_bits[i] > (1ull << 33) || nb_bits[i] > (1ull << 33)) return GF2X_EINVAL;
         const uint64_t na_w = words_of(na_bits[i]), nb_w = words_of(nb_bits[i]);
+        if (std::min(na_w, nb_w) <= (uint64_t)kSmallWords) {
+            direct.push_back(i);
+            continue;
+        }
         const int M = log2_ceil(std::max<uint64_t>(2, na_w + nb_w - 1));
         if (M > kMaxLogN) return GF2X_EINVAL;
         groups[std::make_tuple(M, log2_ceil(na_w), log2_ceil(nb_w))].push_back(i);
@@ -96,6 +103,18 @@ int batch_build(gf2x_batch *B, int count, const uint64_t *na_bits, const uint64_
             B->chunks.push_back(ch);
         }
     }
+    for (size_t c0 = 0; c0 < direct.size(); c0 += 65535) {
+        gf2x_batch::Chunk ch;
+        ch.first = (int)B->order.size();
+        ch.count = (int)std::min<size_t>(65535, direct.size() - c0);
+        ch.max_out_words = 0;
+        for (int q = 0; q < ch.count; q++) {
+            const int i = direct[c0 + q];
+            B->order.push_back(i);
+            ch.max_out_words = std::max(ch.max_out_words, gf2x_out_words(B->na[i], B->nb[i]));
+        }
+        B->chunks.push_back(ch);
+    }
     return GF2X_OK;
 }
 
@@ -120,6 +139,15 @@ int enqueue_chunks(const gf2x_batch *B, const OperandDesc *da, const OperandDesc
     const OperandDesc none_in{nullptr, 0, 0};
     const OutputDesc none_out{nullptr, 0, 0};
     for (const auto &ch : B->chunks) {
+        if (!ch.plan) {
+            launch_mul_small_many(da + ch.first, db + ch.first, dout + ch.first, ch.count,
+                                  ch.max_out_words, s);
+            if (hook) {
+                hook->begin(ST_OUT);
+                hook->end(1);
+            }
+            continue;
+        }
         rc = plan_run_batch(ch.plan.get(), ch.count, da + ch.first, db + ch.first, dout + ch.first,
                             none_in, none_in, none_out, ch.max_out_words, ws, ch.plan->ws_bytes, s,
                             T, st, hook);
@@ -312,6 +340,117 @@ int gf2x_batch_destroy(gf2x_batch *B) {
     cudaGetLastError();
     delete B;
     return GF2X_OK;
+}
+
+int gf2x_batch_tune(gf2x_batch *B, int reps, double *ms_before, double *ms_after) {
+    if (!B || !ms_before || !ms_after) return GF2X_EINVAL;
+    if (reps <= 0) reps = 2;
+    try {
+        std::lock_guard<std::mutex> lk(B->mu);
+        if (!B->launched) return GF2X_EINVAL;  // the descriptors come from an execution
+        if (cudaEventSynchronize(B->done) != cudaSuccess) {
+            cudaGetLastError();
+            return GF2X_ECUDA;
+        }
+        const DevTables *T;
+        int rc = api::tables(&T);
+        if (rc) return rc;
+        int *st = nullptr;
+        if ((rc = api::take_status(&st))) return rc;
+        cudaStream_t s = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaMemsetAsync(st, 0, sizeof(int), s);
+        const OperandDesc none_in{nullptr, 0, 0};
+        const OutputDesc none_out{nullptr, 0, 0};
+        // one group's grouped launch with plan p: device time per execution
+        auto trial = [&](const gf2x_batch::Chunk &ch, const gf2x_plan *p, double *ms) -> int {
+            for (int r = 0; r <= reps; r++) {
+                if (r == 1) cudaEventRecord(e0, s);
+                if (plan_run_batch(p, ch.count, B->d_a + ch.first, B->d_b + ch.first,
+                                   B->d_out + ch.first, none_in, none_in, none_out,
+                                   ch.max_out_words, B->ws, p->ws_bytes, s, T, st, nullptr))
+                    return GF2X_ECUDA;
+            }
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaGetLastError();
+                return GF2X_ECUDA;
+            }
+            float f = 0;
+            cudaEventElapsedTime(&f, e0, e1);
+            *ms = f / reps;
+            return GF2X_OK;
+        };
+        double before = 0, after = 0;
+        for (auto &ch : B->chunks) {
+            if (!ch.plan || rc) continue;
+            const int i0 = B->order[ch.first];
+            double best_ms;
+            if ((rc = trial(ch, ch.plan.get(), &best_ms))) break;
+            before += best_ms;
+            std::shared_ptr<gf2x_plan> best = ch.plan;
+            // the fusion depths that change the strided-pass count, both tile
+            // bufferings, then the BasisCvt tile shape with the best of those;
+            // a candidate whose workspace exceeds the batch's is skipped
+            std::vector<PlanTune> cands;
+            for (int d = 7; d >= 4; d--)
+                for (int nb = 2; nb >= 1; nb--) {
+                    PlanTune t = ch.plan->tune;
+                    t.fft_depth = d;
+                    t.fft_nbuf = nb;
+                    cands.push_back(t);
+                }
+            for (int pass = 0; pass < 2 && !rc; pass++) {
+                if (pass == 1) {
+                    cands.clear();
+                    const int tiles[4] = {10, 11, 12, 13}, thr[3] = {128, 256, 512};
+                    for (int a = 0; a < 4; a++)
+                        for (int b2 = 0; b2 < 3; b2++) {
+                            PlanTune t = best->tune;
+                            t.bcvt.tile_min_log = tiles[a];
+                            t.bcvt.small_threads = thr[b2];
+                            cands.push_back(t);
+                        }
+                }
+                for (const PlanTune &t : cands) {
+                    std::shared_ptr<gf2x_plan> p;
+                    if (api::make_plan(B->na[i0], B->nb[i0], t, &p)) continue;
+                    if (p->ws_bytes * (size_t)ch.count > B->ws_bytes) continue;
+                    double ms;
+                    if ((rc = trial(ch, p.get(), &ms))) break;
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = p;
+                    }
+                }
+            }
+            ch.plan = best;
+            after += best_ms;
+        }
+        cudaStreamSynchronize(s);
+        const int ds = api::read_status(st);
+        api::give_status(st);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaStreamDestroy(s);
+        if (rc) return rc;
+        if (ds) return ds;
+        // the next execution captures the graph again with the chosen plans
+        if (B->exec) {
+            cudaGraphExecDestroy(B->exec);
+            B->exec = nullptr;
+        }
+        *ms_before = before;
+        *ms_after = after;
+        return GF2X_OK;
+    } catch (const std::bad_alloc &) {
+        return GF2X_ENOMEM;
+    } catch (...) {
+        return GF2X_ECUDA;
+    }
 }
 
 int gf2x_batch_status(gf2x_batch *B) {

@@ -26,12 +26,20 @@
 #include "api_internal.h"
 #include "kernels.h"
 #include "plan.h"
+#include "small.h"
 
 using namespace gf2x;
 
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+// How a request is computed: one transform, grouped with the queued requests
+// of the same transform shape (kGroup); by chunks of the longer operand
+// against one transform of the shorter (kChunked, alone); directly without a
+// transform when the shorter operand has at most kSmallWords words (kDirect,
+// grouped with the other direct requests).
+enum Path { kGroup = 0, kChunked = 1, kDirect = 2 };
 
 struct Request {
     uint64_t ticket;
@@ -40,6 +48,10 @@ struct Request {
     uint64_t na, nb;
     std::tuple<int, int, int> shape;
     Clock::time_point t_submit;
+    int path = kGroup;
+    bool swap = false;  // kChunked: the chunks are cut from b (x = b, y = a)
+    ChunkShape cs;
+    std::shared_ptr<gf2x_plan> cplan;  // kChunked: the chunk plan
 };
 
 // First-fit allocator over [0, size) of a device arena (offsets 256-aligned).
@@ -160,20 +172,26 @@ void worker_main(gf2x_server *S) {
             if (!free_slot) break;
             const Request head = S->queue.front();
             std::shared_ptr<gf2x_plan> plan;
-            int rc = api::plan_for(head.na, head.nb, &plan);
+            int rc = head.path == kGroup ? api::plan_for(head.na, head.nb, &plan) : GF2X_OK;
             if (rc) {
                 S->status[head.ticket] = rc;
                 S->queue.pop_front();
                 S->cv_done.notify_all();
                 continue;
             }
+            // workspace per request of the group: the plan's, the chunked
+            // product's, or none for direct products (one arena unit)
+            const size_t per_req = head.path == kGroup ? plan->ws_bytes
+                                   : head.path == kChunked ? chunked_ws_bytes(head.cplan.get(), head.cs.C)
+                                                           : 256;
             std::vector<size_t> take{0};
-            for (size_t q = 1; q < S->queue.size() && take.size() < (size_t)S->max_batch; q++)
-                if (S->queue[q].shape == head.shape) take.push_back(q);
+            if (head.path != kChunked)
+                for (size_t q = 1; q < S->queue.size() && take.size() < (size_t)S->max_batch; q++)
+                    if (S->queue[q].shape == head.shape) take.push_back(q);
             // largest batch whose workspace fits the free arena memory now
             size_t off = 0;
             size_t k = take.size();
-            while (k > 0 && !S->arena.alloc(k * plan->ws_bytes, &off)) k = k > 1 ? k / 2 : 0;
+            while (k > 0 && !S->arena.alloc(k * per_req, &off)) k = k > 1 ? k / 2 : 0;
             if (k == 0) break;  // wait for memory (head-of-line order kept)
             take.resize(k);
             Slot &sl = *free_slot;
@@ -181,7 +199,7 @@ void worker_main(gf2x_server *S) {
             for (size_t q : take) sl.reqs.push_back(S->queue[q]);
             for (size_t q = take.size(); q-- > 0;) S->queue.erase(S->queue.begin() + take[q]);
             sl.off = off;
-            sl.bytes = k * plan->ws_bytes;
+            sl.bytes = k * per_req;
             uint64_t max_words = 0;
             for (size_t q = 0; q < k; q++) {
                 const Request &r = sl.reqs[q];
@@ -202,11 +220,30 @@ void worker_main(gf2x_server *S) {
                                 sl.stream);
                 const OperandDesc none_in{nullptr, 0, 0};
                 const OutputDesc none_out{nullptr, 0, 0};
-                rc = plan_run_batch(plan.get(), (int)k, sl.d_a, sl.d_b, sl.d_out, none_in, none_in,
-                                    none_out, max_words, S->arena_base + off, plan->ws_bytes,
-                                    sl.stream, T, sl.d_st, nullptr)
-                         ? GF2X_ECUDA
-                         : GF2X_OK;
+                if (head.path == kGroup) {
+                    rc = plan_run_batch(plan.get(), (int)k, sl.d_a, sl.d_b, sl.d_out, none_in,
+                                        none_in, none_out, max_words, S->arena_base + off,
+                                        plan->ws_bytes, sl.stream, T, sl.d_st, nullptr)
+                             ? GF2X_ECUDA
+                             : GF2X_OK;
+                } else if (head.path == kChunked) {
+                    const Request &r = sl.reqs[0];
+                    const uint64_t *x = r.swap ? r.b : r.a, *y = r.swap ? r.a : r.b;
+                    const uint64_t xb = r.swap ? r.nb : r.na, yb = r.swap ? r.na : r.nb;
+                    rc = plan_run_chunked(r.cplan.get(), r.cs, x, xb, y, yb, r.out,
+                                          S->arena_base + off, sl.stream, T, sl.d_st, nullptr)
+                             ? GF2X_ECUDA
+                             : GF2X_OK;
+                } else {
+                    for (const Request &r : sl.reqs) {
+                        const uint64_t ow = gf2x_out_words(r.na, r.nb);
+                        if (words_of(r.nb) <= words_of(r.na))
+                            launch_mul_small(r.a, r.na, r.b, r.nb, r.out, ow, 0, false, sl.stream);
+                        else
+                            launch_mul_small(r.b, r.nb, r.a, r.na, r.out, ow, 0, false, sl.stream);
+                    }
+                    rc = cudaGetLastError() == cudaSuccess ? GF2X_OK : GF2X_ECUDA;
+                }
                 if (!rc)
                     cudaMemcpyAsync(sl.h_st, sl.d_st, sizeof(int), cudaMemcpyDeviceToHost, sl.stream);
             }
@@ -315,10 +352,24 @@ int gf2x_server_submit(gf2x_server *S, const uint64_t *a, uint64_t na_bits, cons
         }
         const uint64_t na_w = words_of(na_bits), nb_w = words_of(nb_bits);
         const int M = log2_ceil(std::max<uint64_t>(2, na_w + nb_w - 1));
-        r.shape = std::make_tuple(M, log2_ceil(na_w), log2_ceil(nb_w));
-        std::shared_ptr<gf2x_plan> plan;
-        if ((rc = api::plan_for(na_bits, nb_bits, &plan))) return rc;
-        if (plan->ws_bytes > S->arena.size) return GF2X_EINVAL;  // could never be admitted
+        size_t need = 0;
+        if (std::min(na_w, nb_w) <= (uint64_t)kSmallWords) {
+            r.path = kDirect;
+            r.shape = std::make_tuple(-2, 0, 0);
+            need = 256;
+        } else if (chunk_shape(na_w, nb_w, &r.cs) || (r.swap = chunk_shape(nb_w, na_w, &r.cs))) {
+            r.path = kChunked;
+            const uint64_t y_bits = r.swap ? na_bits : nb_bits;
+            if ((rc = api::plan_for(y_bits, 64 * r.cs.L, &r.cplan))) return rc;
+            r.shape = std::make_tuple(-1, M, 0);
+            need = chunked_ws_bytes(r.cplan.get(), r.cs.C);
+        } else {
+            r.shape = std::make_tuple(M, log2_ceil(na_w), log2_ceil(nb_w));
+            std::shared_ptr<gf2x_plan> plan;
+            if ((rc = api::plan_for(na_bits, nb_bits, &plan))) return rc;
+            need = plan->ws_bytes;
+        }
+        if (need > S->arena.size) return GF2X_EINVAL;  // could never be admitted
         if (!S->any) {
             S->t_first = r.t_submit;
             S->any = true;

@@ -67,7 +67,61 @@ __global__ void __launch_bounds__(256) k_mul_small(const uint64_t *__restrict__ 
     }
 }
 
+// The same for `count` products of a batch, product y (blockIdx.y) read
+// from the descriptors (the shorter operand, at most kSmallWords words,
+// multiplies the longer); the output gets dout[y].words words.
+__global__ void __launch_bounds__(256) k_mul_small_many(const OperandDesc *__restrict__ da,
+                                                        const OperandDesc *__restrict__ db,
+                                                        const OutputDesc *__restrict__ dout) {
+    __shared__ uint64_t ys[kSmallWords];
+    const OperandDesc A = da[blockIdx.y], B = db[blockIdx.y];
+    const OutputDesc O = dout[blockIdx.y];
+    const bool b_short = B.nw <= A.nw;
+    const OperandDesc X = b_short ? A : B, Y = b_short ? B : A;
+    const int yw = (int)Y.nw;
+    if ((int)threadIdx.x < yw) {
+        uint64_t v = Y.src[threadIdx.x];
+        if ((int)threadIdx.x == yw - 1) v &= Y.mask;
+        ys[threadIdx.x] = v;
+    }
+    __syncthreads();
+    constexpr int K = kWordsPerThread;
+    const uint64_t nprod = O.words;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t * K < nprod;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t j0 = t * K;
+        uint64_t acc[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) acc[k] = 0;
+        for (int i = 0; i < yw; i++) {
+            const uint64_t yi = ys[i];
+#pragma unroll
+            for (int k = -1; k < K; k++) {
+                const int64_t q = (int64_t)j0 - i + k;
+                if (q < 0 || (uint64_t)q >= X.nw) continue;
+                uint64_t xv = __ldg(X.src + q);
+                if ((uint64_t)q == X.nw - 1) xv &= X.mask;
+                uint64_t lo, hi;
+                clmul64(xv, yi, lo, hi);
+                if (k >= 0) acc[k] ^= lo;
+                if (k + 1 < K) acc[k + 1] ^= hi;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; k++)
+            if (j0 + k < nprod) O.out[j0 + k] = acc[k];
+    }
+}
+
 }  // namespace
+
+void launch_mul_small_many(const OperandDesc *da, const OperandDesc *db, const OutputDesc *dout,
+                           int count, uint64_t max_words, cudaStream_t s) {
+    if (count <= 0) return;
+    const uint64_t threads = (max_words + kWordsPerThread - 1) / kWordsPerThread;
+    const unsigned gx = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((threads + 255) / 256, 1024));
+    k_mul_small_many<<<dim3(gx, (unsigned)count), 256, 0, s>>>(da, db, dout);
+}
 
 void launch_mul_small(const uint64_t *x, uint64_t x_bits, const uint64_t *y, uint64_t y_bits,
                       uint64_t *out, uint64_t out_limit, uint64_t off, bool accumulate,

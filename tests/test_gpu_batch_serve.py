@@ -87,10 +87,16 @@ def test_batch_chunks_under_small_budget():
 
 def test_server_mix_equals_alone():
     prods = _pairs(13, 60, 6, 18)
-    # a few highly unequal pairs, as in the serving workload
+    # a few highly unequal pairs, as in the serving workload: a short operand
+    # of 16 words (direct products) and operands of 2^14 x 512 words (by
+    # chunks of the longer one), in both orders
     for i in range(4):
         a, b = W.operand_pair(77 + i, 1 << 18, 1 << 10)
         prods.append((a, 1 << 18, b, 1 << 10))
+    for i in range(2):
+        a, b = W.operand_pair(90 + i, 1 << 20, (1 << 15) - 3)
+        prods.append((a, 1 << 20, b, (1 << 15) - 3) if i == 0 else (b, (1 << 15) - 3, a, 1 << 20))
+    assert G.gf2x_product_path(1 << 20, (1 << 15) - 3)[0] == 1
     sv = G.gf2x_server_create(256 << 20, 4)
     try:
         da = [to_dev(p[0]) for p in prods]
@@ -144,3 +150,29 @@ def test_server_memory_admission_and_limits():
         assert e.value.status == G.GF2X_EINVAL
     finally:
         G.gf2x_server_destroy(sv)
+
+
+def test_batch_tuned_in_batch_context():
+    prods = _pairs(14, 48, 10, 18)
+    na = [p[1] for p in prods]
+    nb = [p[3] for p in prods]
+    batch = G.gf2x_batch_create(na, nb, 256 << 20)
+    try:
+        da = [to_dev(p[0]) for p in prods]
+        db = [to_dev(p[2]) for p in prods]
+        outs = [empty_dev(G.gf2x_out_words(p[1], p[3])) for p in prods]
+        s = torch.cuda.Stream()
+        with pytest.raises(G.GF2XError):  # nothing to tune on before an execution
+            G.gf2x_batch_tune(batch, 1)
+        G.gf2x_batch_execute(batch, da, db, outs, s)
+        before, after = G.gf2x_batch_tune(batch, 1)
+        assert 0 < after <= before
+        for o in outs:
+            o.zero_()
+        G.gf2x_batch_execute(batch, da, db, outs, s)  # the tuned plans, captured again
+        G.gf2x_batch_status(batch)
+        for p, o in zip(prods, outs):
+            want = P.mul(p[0], p[1], p[2], p[3])
+            assert np.array_equal(from_dev(o, len(want)), want), (p[1], p[3])
+    finally:
+        G.gf2x_batch_destroy(batch)
