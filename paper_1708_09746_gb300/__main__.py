@@ -1,6 +1,7 @@
 """Multiply two seeded random operands on cuda:0 and print the time per product.
 
     python -m paper_1708_09746_gb300 --log-bits 28 --reps 2 [--plan 7 2 11 256]
+                                     [--form tower|tower256|simple|frobenius]
 
 Each operand has 2^log_bits bits (top bit set, uniform otherwise, seed 1).  The
 first product is a warm-up (it builds the plan and the tables); the command
@@ -27,6 +28,10 @@ def main():
                    help="plan parameters of the shape (gf2x_tune_set) instead of the defaults")
     p.add_argument("--autotune", action="store_true",
                    help="run gf2x_autotune for the shape first and print its choice")
+    p.add_argument("--form", default="tower", choices=["tower", "tower256", "simple", "frobenius"],
+                   help="the form of the method: tower field F~_{2^128} with 64-bit blocks "
+                        "(gf2x_mul), F~_{2^256} with 128-bit blocks, the simple polynomial-"
+                        "basis form, or the Frobenius partition")
     args = p.parse_args()
     _build.build()
     import paper_1708_09746_gb300 as G
@@ -43,11 +48,14 @@ def main():
     if args.autotune:
         print("autotune:", G.gf2x_autotune(na, nb))
     torch.cuda.synchronize()
+    fn = {"tower": G.gf2x_mul, "tower256": G.gf2x_mul_tower256, "simple": G.gf2x_mul_simple,
+          "frobenius": G.gf2x_mul_frobenius}[args.form]
     for i in range(args.reps):
         t0 = time.perf_counter()
-        G.gf2x_mul(da, na, db, nb, out)
+        fn(da, na, db, nb, out)
         torch.cuda.synchronize()
-        print("product %d: %d x %d bits, %.3f ms" % (i, na, nb, 1e3 * (time.perf_counter() - t0)))
+        print("product %d (%s): %d x %d bits, %.3f ms" % (i, args.form, na, nb,
+                                                      1e3 * (time.perf_counter() - t0)))
 
 
 if __name__ == "__main__":

@@ -190,14 +190,24 @@ __device__ __forceinline__ uint64_t step_word(const uint64_t *f, uint64_t nwords
     return f[w] ^ (bits64(f, nwords, 64 * w + (E - e)) & m);
 }
 
-// One step of one level over the whole array, in place (the step reads only
-// bits it does not write).
+// One step of one level with segments of at least 128 bits, in place (the
+// step reads only bits it does not write).  Only the words holding the step's
+// destination bits are visited: per segment of 2E bits, words [0, E/64) for
+// step 2 (destination [e, E)) and the words of [E, E + e) for step 1.
 __global__ void __launch_bounds__(256) k_bitcvt_step(uint64_t *f, uint64_t nwords, int logE, int loge,
                                                      int step) {
-    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < nwords;
-         w += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t v = step_word(f, nwords, w, logE, loge, step);
-        f[w] = v;
+    const uint64_t E = 1ull << logE, e = 1ull << loge, D = E - e;
+    const uint64_t seg_words = (2 * E) >> 6;
+    const uint64_t first = step == 1 ? (E >> 6) : 0;
+    const uint64_t count = step == 1 ? ((E + e + 63) >> 6) - (E >> 6) : (E >> 6);
+    const uint64_t lo = step == 1 ? E : e, hi = step == 1 ? E + e : E;
+    const uint64_t total = (nwords / seg_words) * count;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t seg = t / count, k = t - seg * count;
+        const uint64_t w = seg * seg_words + first + k;
+        const uint64_t m = seg_mask(w, logE, lo, hi);
+        if (m) f[w] ^= bits64(f, nwords, 64 * w + D) & m;
     }
 }
 
@@ -280,7 +290,10 @@ uint64_t run_bit_cvt(uint64_t *f, int L, int inverse, cudaStream_t s) {
         flush();
         for (int h = 0; h < 2; h++) {
             const int step = inverse ? 2 - h : 1 + h;
-            k_bitcvt_step<<<grid_of(nwords, 256), 256, 0, s>>>(f, nwords, l.logE, l.loge, step);
+            const uint64_t E = 1ull << l.logE, e = 1ull << l.loge;
+            const uint64_t per_seg = step == 1 ? ((E + e + 63) >> 6) - (E >> 6) : (E >> 6);
+            const uint64_t items = (nwords / ((2 * E) >> 6)) * per_seg;
+            k_bitcvt_step<<<grid_of(items, 256), 256, 0, s>>>(f, nwords, l.logE, l.loge, step);
             launches++;
         }
     }
@@ -305,11 +318,46 @@ __device__ __forceinline__ uint4 tab16(const uint4 *__restrict__ tab, const uint
     return acc;
 }
 
+// 32 x 32 bit transpose across a warp: lane l holds row l, and afterwards
+// holds column l (bit j = bit l of row j).  Stage s swaps the off-diagonal
+// blocks of size s between lanes l and l ^ s.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, unsigned lane) {
+    const uint32_t m[5] = {0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu, 0x0000FFFFu};
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        const int sh = 1 << k;
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, sh);
+        x = (lane & sh) ? ((x & ~m[k]) | ((y & ~m[k]) >> sh)) : ((x & m[k]) | ((y & m[k]) << sh));
+    }
+    return x;
+}
+
 // Element i (i < n) = sum_j g[i + j n] w_j over the bits of the 2^L-bit array
-// g (bits at positions >= nbits are zero).
+// g (bits at positions >= nbits are zero).  With n >= 32 (a multiple of 32)
+// the bits of the warp's 32 consecutive elements in row j are one aligned
+// 32-bit word: lane l loads rows l, l+32, l+64, l+96 and a warp transpose
+// hands every lane its element's 128-bit column.
 __global__ void __launch_bounds__(256) k_encode(const uint64_t *__restrict__ g, uint64_t nbits,
                                                 uint64_t n, uint4 *E, const uint4 *__restrict__ enc) {
     const uint64_t rows = std::min<uint64_t>(128, (nbits + n - 1) / n);
+    if (n >= 32) {
+        const uint32_t *g32 = reinterpret_cast<const uint32_t *>(g);
+        const unsigned lane = threadIdx.x & 31;
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+             i += (uint64_t)gridDim.x * blockDim.x) {
+            const uint64_t i0 = i - lane;
+            uint32_t v[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint64_t j = 32 * q + lane;
+                const uint64_t pos = j * n + i0;
+                const uint32_t row = (j < rows && pos < nbits) ? __ldg(g32 + (pos >> 5)) : 0u;
+                v[q] = warp_transpose32(row, lane);
+            }
+            E[i] = tab16(enc, v);
+        }
+        return;
+    }
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t v[4] = {0, 0, 0, 0};
@@ -340,11 +388,13 @@ __global__ void __launch_bounds__(256) k_decode(const uint4 *__restrict__ E, uin
         }
         const uint32_t cw[4] = {col.x, col.y, col.z, col.w};
         if (n >= 32) {
+            // the warp transpose turns the 32 columns back into rows: lane l
+            // stores rows l, l+32, l+64, l+96 of the warp's 32 elements
             const uint64_t i0 = i - lane;
-#pragma unroll 4
-            for (int j = 0; j < 128; j++) {
-                const uint32_t word = __ballot_sync(0xffffffffu, (cw[j >> 5] >> (j & 31)) & 1u);
-                if (lane == 0) c32[((uint64_t)j * n + i0) >> 5] = word;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint32_t row = warp_transpose32(cw[q], lane);
+                c32[((uint64_t)(32 * q + lane) * n + i0) >> 5] = row;
             }
         } else if (i < n) {
             for (int j = 0; j < 128; j++)
