@@ -352,8 +352,15 @@ __device__ __forceinline__ void bcvt_op(T *s, uint32_t tile, const BcvtOp &op) {
 // by c - lo (the steps in `lb` are given in tile-local form).
 // SMALL: launched with at most 256 threads and 64 KiB of shared memory; for
 // 64-bit coefficients four such CTAs share an SM (64 registers per thread).
+// 128-bit tiles of at most 64 KiB: at most 85 registers per thread so that three
+// 256-thread CTAs share an SM (iBasisCvt 0.41 -> 0.37 ms at 2^28; four CTAs,
+// 64 registers, spill and come to 0.39 ms).
+#ifndef GF2X_BCVT128_MINB
+#define GF2X_BCVT128_MINB 3
+#endif
 template <typename T, bool SMALL>
-__global__ void __launch_bounds__(SMALL ? 256 : 512, (SMALL && sizeof(T) == 8) ? 4 : 1)
+__global__ void __launch_bounds__(SMALL ? 256 : 512,
+                                  SMALL ? (sizeof(T) == 8 ? 4 : GF2X_BCVT128_MINB) : 1)
     k_bcvt_tile(T *f, int c, int lo, int w, LevelBatch lb,
                                                       int inverse, uint64_t stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
