@@ -386,9 +386,13 @@ def measure_sizes(G, torch, W, dev, stream, flush):
         stream.synchronize()
         ms = [e0.elapsed_time(e1) for e0, e1 in evs[1:]]
         N = G.gf2x_fft_points(na, nb)
+        # the whole-path byte model (240 N) describes one transform of N points;
+        # chunked, direct and split products move other amounts
+        frac = (240 * N / (sum(ms) / len(ms) / 1e3) / 1e9 / _peaks().get("hbm_gbs", 6800.0)
+                if path == 0 else None)
         res[name] = {"bits": [na, nb], "ms": sum(ms) / len(ms), "fft_points": N,
-                     "path_hbm_frac": 240 * N / (sum(ms) / len(ms) / 1e3) / 1e9 /
-                     _peaks().get("hbm_gbs", 6800.0), "plan": tuned}
+                     "path": ["one transform", "chunked", "direct", "tail split"][path],
+                     "path_hbm_frac": frac, "plan": tuned}
         del da, db, out
         torch.cuda.empty_cache()
     return res
