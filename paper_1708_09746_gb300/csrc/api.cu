@@ -685,6 +685,7 @@ int gf2x_mul_host(const uint64_t *a_host, uint64_t na_bits, const uint64_t *b_ho
         cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
         size_t ba = 8 * words_of(na_bits), bb = 8 * words_of(nb_bits);
         size_t bo = 8 * gf2x_out_words(na_bits, nb_bits);
+        if (overlap(out_host, bo, a_host, ba) || overlap(out_host, bo, b_host, bb)) return GF2X_EINVAL;
         std::shared_ptr<gf2x_plan> p;
         if ((rc = cached_plan(na_bits, nb_bits, &p))) return rc;
         cudaStream_t cs;

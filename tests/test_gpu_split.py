@@ -90,3 +90,20 @@ def test_fullsize_split_and_direct(name):
     for _ in range(3):
         r = P.random_irreducible64(rng)
         assert P.fingerprint_ok(a, na, b, nb, c, r)
+
+
+def test_host_call_with_pinned_buffers():
+    # page-locked and pageable host buffers (staged copies on the library's
+    # streams either way)
+    for na, nb in [((1 << 20) + 77, (1 << 19) + 5), (1 << 22, 1 << 22)]:
+        a, b = W.operand_pair(na % 97, na, nb)
+        ow = G.gf2x_out_words(na, nb)
+        ha = torch.from_numpy(a.view(np.int64).copy()).pin_memory()
+        hb = torch.from_numpy(b.view(np.int64).copy()).pin_memory()
+        ho = torch.full((ow,), -1, dtype=torch.int64).pin_memory()
+        G.gf2x_mul_host(ha, na, hb, nb, ho)
+        want = P.mul(a, na, b, nb)
+        assert np.array_equal(ho.numpy().view(np.uint64), want)
+        ho2 = np.full(ow, 7, dtype=np.uint64)   # pageable output
+        G.gf2x_mul_host(ha, na, hb, nb, ho2)
+        assert np.array_equal(ho2, want)
