@@ -39,7 +39,17 @@ sys.path.insert(0, ROOT)
 METRIC = ("ms per 2^28-bit GF(2)[x] product (% HBM roofline); "
           "batched products/s vs one-by-one")
 PAPER_MS_2_28 = 2302.0  # Table 2, F~_{2^128} tower row, 2^28-bit operands (Haswell)
-SHFL_PER_LIMB_MUL = 7   # warp shuffles per F~_{2^32} limb product (5-bit windows)
+# warp shuffles per F~_{2^32} limb product (5-bit windows): seven in the strided
+# FFT passes, six in the bottom passes (the 2-bit window on the integer pipe)
+SHFL_STRIDED, SHFL_BOTTOM, FFT_TILE_LOG = 7, 6, 12
+
+
+def shfl_per_limb_mul(M, la, lb):
+    """Average shuffles per limb product over the computed layers of one
+    product: the layers below 2^12 of each transform run in the bottom pass."""
+    bottom = min(la, FFT_TILE_LOG) + min(lb, FFT_TILE_LOG) + min(M, FFT_TILE_LOG)
+    strided = (la + lb + M) - bottom
+    return (SHFL_BOTTOM * bottom + SHFL_STRIDED * strided) / max(1, bottom + strided)
 
 
 def _args():
@@ -701,7 +711,8 @@ def run_ours(args):
         probe = {"error": str(e)}
     shfl_rate = probe.get("shfl_per_clk_sm") or 1.0
     sms = probe.get("sms") or 152
-    peak_lmul = sms * shfl_rate * 32 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / SHFL_PER_LIMB_MUL
+    spl = shfl_per_limb_mul(M, la, lb)
+    peak_lmul = sms * shfl_rate * 32 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / spl
     ach_lmul = work / (fft_ms / 1e3)
     traffic = fft_traffic_per_launch()
     # The dominant kernel against the HBM roofline, bytes from the path's byte
@@ -729,17 +740,18 @@ def run_ours(args):
                            "one global + one local pass per forward transform, the local pass "
                            "of b also reading FFT(a), one inverse global pass"}
     roof_alu = {"bound": "alu", "kernel": "k_fft_pass",
-            "note": "ceiling of the current butterfly method (7 warp shuffles per F~_{2^32} "
-                    "limb product), not of the chip or the algorithm",
+            "note": "ceiling of the current butterfly method (%.2f warp shuffles per "
+                    "F~_{2^32} limb product: 7 in strided passes, 6 in bottom passes), not of "
+                    "the chip or the algorithm" % spl,
             "achieved": ach_lmul / 1e9, "peak": peak_lmul / 1e9,
             "unit": "G limb-mult/s", "frac": ach_lmul / peak_lmul,
             "work_per_launch": work / n_launch,
             "peak_source": ("measured shuffle issue rate (gf2x_probe_pipes: %.3f warp shuffles "
-                            "per SM clock) x %d SMs x 32 lanes x max SM clock / 7 shuffles per "
-                            "F~_{2^32} limb product" % (shfl_rate, sms))
+                            "per SM clock) x %d SMs x 32 lanes x max SM clock / %.2f shuffles per "
+                            "F~_{2^32} limb product" % (shfl_rate, sms, spl))
             if "shfl_per_clk_sm" in probe else
-            "derived: 152 SMs x 32 lanes x max SM clock / 7 warp shuffles per F~_{2^32} "
-            "limb product (probe failed: %s)" % probe.get("error"),
+            "derived: 152 SMs x 32 lanes x max SM clock / %.2f warp shuffles per F~_{2^32} "
+            "limb product (probe failed: %s)" % (spl, probe.get("error")),
             "pipe_probe": probe}
     plan_depth = max(1, min(7, int(tuned.get("fft_depth", 7))))
     fbytes = fft_hbm_bytes(N, M, la, lb, plan_depth)

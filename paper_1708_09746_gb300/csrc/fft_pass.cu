@@ -21,10 +21,13 @@
 //    share the multiplier (column bits plus lower rows span >= 5 index bits):
 //    whole elements in registers, up to three rows per register sub-pass,
 //    warp-shuffle tables (the table of cval[r] is built once per tile, the
-//    table of d is precomputed; the table of their sum is the XOR of the two);
+//    table of d is precomputed; the table of their sum is the XOR of the two;
+//    seven shuffles per 32-bit limb in the strided passes, six in the bottom
+//    pass with the top two bits on the integer pipe);
 //  * rows 3-5 of the bottom pass: one limb-wise sub-pass (a lane holds one
 //    32-bit limb of 8 elements, so a warp's lanes share the multiplier of a
-//    group of up to 64 elements) with the same shuffle tables;
+//    group of up to 64 elements) with the same shuffle tables, the tables of
+//    a group's other blocks as block 0's plus precomputed offsets;
 //  * rows 0-2 of a bottom tile of at least 2^8 elements: one register
 //    sub-pass per lane group of 8 elements; the multiplier's warp-uniform part
 //    through the shuffle tables, its per-lane F~_{2^8} part through a per-lane
@@ -32,6 +35,7 @@
 //  * lane-varying rows of smaller tiles: the F~_{2^8} product table in shared
 //    memory, one row per sweep.
 #include <algorithm>
+#include <cstddef>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -46,6 +50,10 @@
 
 namespace gf2x {
 
+// shfl6_table_sum reads words 194, 195 of each seven-word shuffle table as one
+// 8-byte load: the rows 0-2 tables must start on 8-byte boundaries too
+static_assert(offsetof(DevTables, low_shfl) % 16 == 0, "low_shfl alignment");
+
 namespace {
 std::atomic<uint32_t> g_wait_spins{kWaitSpins};
 }
@@ -55,11 +63,22 @@ void set_wait_spins(int64_t spins) {
 }
 uint32_t wait_spins() { return g_wait_spins.load(); }
 
+// Which product the register sub-passes use (shfl6_mul128 or shfl_mul128).
+#ifndef GF2X_SHFL6_STRIDED
+#define GF2X_SHFL6_STRIDED 0
+#endif
+#ifndef GF2X_SHFL6_BOTTOM
+#define GF2X_SHFL6_BOTTOM 1
+#endif
+constexpr bool kShfl6Strided = GF2X_SHFL6_STRIDED != 0;
+constexpr bool kShfl6Bottom = GF2X_SHFL6_BOTTOM != 0;
+
 // ---------------------------------------------------------------------------
 // Register sub-pass: G layers (tile rows r_lo .. r_lo+G-1) on columns of 2^G
 // elements held by one thread.  Requires c + r_lo >= 5 so that a warp's lanes
-// differ only in bits below the sub-pass (warp-uniform multipliers).
-template <int G, bool INV>
+// differ only in bits below the sub-pass (warp-uniform multipliers).  SIX: the
+// six-shuffle product (two bits on the integer pipe), else seven shuffles.
+template <int G, bool INV, bool SIX>
 __device__ __forceinline__ void reg_subpass(uint4 *s, int c, int g, int r_lo, int uf,
                                             const uint32_t *ctab, const uint32_t *__restrict__ d_shfl) {
     const int r_hi = r_lo + G - 1;
@@ -82,21 +101,37 @@ __device__ __forceinline__ void reg_subpass(uint4 *s, int c, int g, int r_lo, in
 #pragma unroll
             for (int B = 0; B < (1 << (G - 1 - rr)); B++) {
                 const uint32_t prefix = (hi_rows << (r_hi - r)) | (uint32_t)B;
-                ShflTab T;
-                const uint32_t *dp = d_shfl + (size_t)(off + prefix) * 224 + lane;
-                const uint32_t *cp = ctab + (r - uf) * 224 + lane;
+                const uint32_t *ct = ctab + (r - uf) * 224;
+                const uint32_t *dt = d_shfl + (size_t)(off + prefix) * 224;
+                if constexpr (SIX) {
+                    const ShflTab6 T = shfl6_table_sum(ct, dt, lane);
 #pragma unroll
-                for (int w = 0; w < 7; w++) T.t[w] = cp[32 * w] ^ __ldg(dp + 32 * w);
+                    for (int j = 0; j < (1 << rr); j++) {
+                        uint4 &u = e[B * (2 << rr) + j];
+                        uint4 &v = e[B * (2 << rr) + j + (1 << rr)];
+                        if (!INV) {
+                            u = xor4(u, shfl6_mul128(v, T));
+                            v = xor4(v, u);
+                        } else {
+                            v = xor4(v, u);
+                            u = xor4(u, shfl6_mul128(v, T));
+                        }
+                    }
+                } else {
+                    ShflTab T;
 #pragma unroll
-                for (int j = 0; j < (1 << rr); j++) {
-                    uint4 &u = e[B * (2 << rr) + j];
-                    uint4 &v = e[B * (2 << rr) + j + (1 << rr)];
-                    if (!INV) {
-                        u = xor4(u, shfl_mul128(v, T));
-                        v = xor4(v, u);
-                    } else {
-                        v = xor4(v, u);
-                        u = xor4(u, shfl_mul128(v, T));
+                    for (int w = 0; w < 7; w++) T.t[w] = ct[32 * w + lane] ^ __ldg(dt + 32 * w + lane);
+#pragma unroll
+                    for (int j = 0; j < (1 << rr); j++) {
+                        uint4 &u = e[B * (2 << rr) + j];
+                        uint4 &v = e[B * (2 << rr) + j + (1 << rr)];
+                        if (!INV) {
+                            u = xor4(u, shfl_mul128(v, T));
+                            v = xor4(v, u);
+                        } else {
+                            v = xor4(v, u);
+                            u = xor4(u, shfl_mul128(v, T));
+                        }
                     }
                 }
             }
@@ -106,14 +141,14 @@ __device__ __forceinline__ void reg_subpass(uint4 *s, int c, int g, int r_lo, in
     }
 }
 
-template <bool INV>
+template <bool INV, bool SIX>
 __device__ __forceinline__ void run_subpass(int G, uint4 *s, int c, int g, int r_lo, int uf,
                                             const uint32_t *ctab, const uint32_t *d_shfl) {
     switch (G) {
-        case 1: reg_subpass<1, INV>(s, c, g, r_lo, uf, ctab, d_shfl); break;
-        case 2: reg_subpass<2, INV>(s, c, g, r_lo, uf, ctab, d_shfl); break;
-        case 3: reg_subpass<3, INV>(s, c, g, r_lo, uf, ctab, d_shfl); break;
-        default: reg_subpass<3, INV>(s, c, g, r_lo, uf, ctab, d_shfl); break;
+        case 1: reg_subpass<1, INV, SIX>(s, c, g, r_lo, uf, ctab, d_shfl); break;
+        case 2: reg_subpass<2, INV, SIX>(s, c, g, r_lo, uf, ctab, d_shfl); break;
+        case 3: reg_subpass<3, INV, SIX>(s, c, g, r_lo, uf, ctab, d_shfl); break;
+        default: reg_subpass<3, INV, SIX>(s, c, g, r_lo, uf, ctab, d_shfl); break;
     }
 }
 
@@ -126,12 +161,27 @@ __device__ __forceinline__ void run_subpass(int G, uint4 *s, int c, int g, int r
 // whole elements (Prop. 3.2: the limbs are multiplied independently).  Lane l
 // reads word (element << 2) + (l & 3) of element base + (l >> 2): one
 // conflict-free 128-byte row per value.
+//
+// Row r of a group has 2^(NR-1-(r-3)) butterfly blocks B, and by linearity in
+// the index bits the multiplier of block B is that of block 0 plus d(k, B),
+// the same in every group and tile.  The tables of d(k, 1) and d(k, 2) are
+// read once per call and kept in registers, so that a group reads one table
+// per row instead of one per block.
 template <int NR, bool INV>
 __device__ __forceinline__ void limb_subpass(uint4 *s, int g, int uf, const uint32_t *ctab,
                                              const uint32_t *__restrict__ d_shfl) {
     uint32_t *wds = reinterpret_cast<uint32_t *>(s);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint32_t groups = 1u << (g - 3 - NR);
+    ShflTab6 R[NR][2];  // [row - 3][bit]: the table of d(k, 1 << bit)
+#pragma unroll
+    for (int rr = 0; rr < NR; rr++) {
+        const uint32_t off = (1u << (g - uf)) - (1u << (g - 3 - rr));
+#pragma unroll
+        for (int bit = 0; bit < 2; bit++)
+            if ((2 << bit) <= (1 << (NR - 1 - rr)))
+                R[rr][bit] = shfl6_table(d_shfl + (size_t)(off + (1u << bit)) * 224, lane);
+    }
     for (uint32_t grp = warp; grp < groups; grp += nwarps) {
         uint32_t v[1 << NR];
 #pragma unroll
@@ -142,24 +192,23 @@ __device__ __forceinline__ void limb_subpass(uint4 *s, int g, int uf, const uint
             const int rr = INV ? step : (NR - 1 - step);
             const int r = 3 + rr;
             const uint32_t off = (1u << (g - uf)) - (1u << (g - r));
+            const ShflTab6 T0 = shfl6_table_sum(
+                ctab + (r - uf) * 224, d_shfl + (size_t)(off + (grp << (NR - 1 - rr))) * 224, lane);
 #pragma unroll
             for (int B = 0; B < (1 << (NR - 1 - rr)); B++) {
-                const uint32_t prefix = (grp << (NR - 1 - rr)) | (uint32_t)B;
-                ShflTab T;
-                const uint32_t *dp = d_shfl + (size_t)(off + prefix) * 224 + lane;
-                const uint32_t *cp = ctab + (r - uf) * 224 + lane;
-#pragma unroll
-                for (int w = 0; w < 7; w++) T.t[w] = cp[32 * w] ^ __ldg(dp + 32 * w);
+                ShflTab6 T = T0;
+                if (B & 1) shfl6_xor(T, R[rr][0]);
+                if (B & 2) shfl6_xor(T, R[rr][1]);
 #pragma unroll
                 for (int j = 0; j < (1 << rr); j++) {
                     uint32_t &u = v[B * (2 << rr) + j];
                     uint32_t &x = v[B * (2 << rr) + j + (1 << rr)];
                     if (!INV) {
-                        u ^= shfl_mul32(x, T);
+                        u ^= shfl6_mul32(x, T);
                         x ^= u;
                     } else {
                         x ^= u;
-                        u ^= shfl_mul32(x, T);
+                        u ^= shfl6_mul32(x, T);
                     }
                 }
             }
@@ -210,8 +259,8 @@ __device__ __forceinline__ uint32_t lane_mul32(const uint8_t *lt, uint32_t x) {
 }
 
 template <int R>
-__device__ __forceinline__ uint4 low_mul128(uint4 v, const ShflTab &T, const uint8_t *lt) {
-    const uint4 p = shfl_mul128(v, T);
+__device__ __forceinline__ uint4 low_mul128(uint4 v, const ShflTab6 &T, const uint8_t *lt) {
+    const uint4 p = shfl6_mul128(v, T);
     return make_uint4(p.x ^ lane_mul32<R>(lt, v.x), p.y ^ lane_mul32<R>(lt, v.y),
                       p.z ^ lane_mul32<R>(lt, v.z), p.w ^ lane_mul32<R>(lt, v.w));
 }
@@ -220,13 +269,20 @@ template <int R, bool INV>
 __device__ __forceinline__ void low_row(uint4 (&e)[8], uint32_t blk, const uint32_t *ctab,
                                         const uint32_t *__restrict__ low_shfl, const uint8_t *lt) {
     const int lane = threadIdx.x & 31;
+    // D(R, blk, h) = D(R, blk, 0) + D(R, 0, h): one table per block of 8 and
+    // the tables of D(R, 0, 1) and D(R, 0, 2)
+    constexpr int lo = kLowOff[R];
+    const ShflTab6 T0 =
+        shfl6_table_sum(ctab + R * 224, low_shfl + (size_t)(lo + blk * (4 >> R)) * 224, lane);
+    ShflTab6 H[2];
+#pragma unroll
+    for (int bit = 0; bit < 2; bit++)
+        if ((2 << bit) <= (4 >> R)) H[bit] = shfl6_table(low_shfl + (size_t)(lo + (1 << bit)) * 224, lane);
 #pragma unroll
     for (int h = 0; h < (4 >> R); h++) {
-        ShflTab T;
-        const uint32_t *dp = low_shfl + (size_t)(kLowOff[R] + blk * (4 >> R) + h) * 224 + lane;
-        const uint32_t *cp = ctab + R * 224 + lane;
-#pragma unroll
-        for (int w = 0; w < 7; w++) T.t[w] = cp[32 * w] ^ __ldg(dp + 32 * w);
+        ShflTab6 T = T0;
+        if (h & 1) shfl6_xor(T, H[0]);
+        if (h & 2) shfl6_xor(T, H[1]);
 #pragma unroll
         for (int j = 0; j < (1 << R); j++) {
             uint4 &u = e[h * (2 << R) + j];
@@ -324,6 +380,9 @@ __device__ __forceinline__ void prefetch_tables(const FftPassArgs &a, int tb, co
 }
 
 // Persistent kernel: each CTA walks the tiles blockIdx.x, +gridDim.x, ...
+// Two instantiations: STRIDED for the passes with c > 0 (register sub-passes
+// only), the other for the contiguous bottom passes (limb-wise rows, rows 0-2,
+// changeRepr on the way in, pointmul).
 // with one or two tile buffers.  While one tile is computed, the next one is
 // being loaded by bulk copies (TMA) and the previous one stored; warp 0 issues
 // all copies.  The first strided pass of a transform loads the changeRepr'd
@@ -331,7 +390,12 @@ __device__ __forceinline__ void prefetch_tables(const FftPassArgs &a, int tb, co
 // first reads the 64-bit blocks and applies changeRepr on the way in.  The
 // shuffle tables of the next tile's multipliers are copied in
 // asynchronously while the current tile is computed.
+template <bool STRIDED>
 __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
+    // the register sub-passes' product: six shuffles in the bottom passes,
+    // seven in the strided ones (measured: the strided passes wait on their
+    // table loads, not on the shuffle pipe, and lose with the longer chain)
+    constexpr bool SIX = STRIDED ? kShfl6Strided : kShfl6Bottom;
     extern __shared__ __align__(128) unsigned char smem[];
     const int g = a.g, c = a.c, uf = a.uf;
     // shuffle tables of the tile's multipliers for rows tb .. g-1 (all rows
@@ -380,12 +444,12 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         for (int i = 0; i < 3; i++) mbar_init(&bar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (a.needs_mt) {
+    if (!STRIDED && a.needs_mt) {
         const uint4 *src = reinterpret_cast<const uint4 *>(a.T->mul8);
         uint4 *dst = reinterpret_cast<uint4 *>(mt);
         for (int i = threadIdx.x; i < 4096; i += blockDim.x) dst[i] = __ldg(src + i);
     }
-    if (a.needs_mt || a.low3) {
+    if (!STRIDED && (a.needs_mt || a.low3)) {
         const uint4 *src = reinterpret_cast<const uint4 *>(&a.T->low_lane[0][0]);
         uint4 *dst = reinterpret_cast<uint4 *>(lane_tab);
         for (int i = threadIdx.x; i < (int)(kLaneTabBytes / 16); i += blockDim.x) dst[i] = __ldg(src + i);
@@ -434,7 +498,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         }
         if (threadIdx.x < 32) cval[threadIdx.x] = cnext[threadIdx.x];
         const uint64_t base = tile_base(G, tt);
-        if (from_g) {
+        if (!STRIDED && from_g) {
             const uint64_t *gy = a.g64 + y * a.strideW;
             for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) {
                 const uint64_t idx = base | ((uint64_t)(q >> c) << a.k_lo) | (q & cmask);
@@ -450,10 +514,10 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
         if (a.mode != 1) {  // forward layers g_f-1 .. 0
             for (int r_hi = a.g_f - 1; r_hi >= ul; r_hi -= 3) {
                 const int r_lo = max(ul, r_hi - 2);
-                run_subpass<false>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab_u, a.d_shfl);
+                run_subpass<false, SIX>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab_u, a.d_shfl);
                 __syncthreads();
             }
-            if (ul > uf && a.g_f > uf) {  // rows 3 .. min(g_f, ul) - 1 limb-wise
+            if (!STRIDED && ul > uf && a.g_f > uf) {  // rows 3 .. min(g_f, ul) - 1 limb-wise
                 const int nr = min(a.g_f, ul) - uf;
                 if (nr >= 3)
                     limb_subpass<3, false>(s, g, uf, ctab_u, a.d_shfl);
@@ -463,7 +527,8 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
                     limb_subpass<1, false>(s, g, uf, ctab_u, a.d_shfl);
                 __syncthreads();
             }
-            if (a.low3 && a.g_f >= 3) {  // rows 2, 1, 0 in registers
+            if (STRIDED) {
+            } else if (a.low3 && a.g_f >= 3) {  // rows 2, 1, 0 in registers
                 low3_subpass<false>(s, g, ctab, a.T->low_shfl[0][0], &lane_tab[0]);
                 __syncthreads();
             } else {
@@ -473,7 +538,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
                 }
             }
         }
-        if (a.mode == 2) {  // pointmul with the other operand's transform
+        if (!STRIDED && a.mode == 2) {  // pointmul with the other operand's transform
             for (uint32_t q = threadIdx.x; q < tile; q += blockDim.x) {
                 const uint64_t idx = base | ((uint64_t)(q >> c) << a.k_lo) | (q & cmask);
                 s[q] = mt_gmul128(M, s[q], __ldg(a.FA + y * a.strideFA + idx));
@@ -481,7 +546,8 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
             __syncthreads();
         }
         if (a.mode != 0) {  // inverse layers 0 .. g-1
-            if (a.low3) {  // rows 0, 1, 2 in registers
+            if (STRIDED) {
+            } else if (a.low3) {  // rows 0, 1, 2 in registers
                 low3_subpass<true>(s, g, ctab, a.T->low_shfl[0][0], &lane_tab[0]);
                 __syncthreads();
             } else {
@@ -490,7 +556,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
                     __syncthreads();
                 }
             }
-            if (ul > uf) {  // rows 3 .. ul - 1 limb-wise
+            if (!STRIDED && ul > uf) {  // rows 3 .. ul - 1 limb-wise
                 if (ul - uf >= 3)
                     limb_subpass<3, true>(s, g, uf, ctab_u, a.d_shfl);
                 else
@@ -499,7 +565,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
             }
             for (int r_lo = ul; r_lo < g; r_lo += 3) {
                 const int r_hi = min(g - 1, r_lo + 2);
-                run_subpass<true>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab_u, a.d_shfl);
+                run_subpass<true, SIX>(r_hi - r_lo + 1, s, c, g, r_lo, uf, ctab_u, a.d_shfl);
                 __syncthreads();
             }
         }
@@ -654,6 +720,10 @@ int make_pass(int k_lo, int g, int c, int uf, int mode, int g_f, PassTableFn src
     if (uf < g && c + uf < 5 && !limb34) return -1;
     int rc = (src ? src : cached_pass_tables)(k_lo, g, uf, &p->d_val, &p->d_shfl);
     if (rc) return rc;
+    // the passes read two words of each shuffle table as one 8-byte load
+    // (shfl6_table_sum): a table array that does not start on a 16-byte
+    // boundary is refused here rather than launched
+    if (reinterpret_cast<uintptr_t>(p->d_shfl) & 15) return -3;
     p->k_lo = k_lo;
     p->g = g;
     p->c = c;
@@ -742,7 +812,8 @@ int plan_fft_fused(int M, int log_p, PassList &fwd_global, FftPassCfg &local, Pa
 }
 
 void prepare_fft_attributes() {
-    ensure_smem_attr(reinterpret_cast<const void *>(k_fft_pass), 227 * 1024);
+    ensure_smem_attr(reinterpret_cast<const void *>(k_fft_pass<false>), 227 * 1024);
+    ensure_smem_attr(reinterpret_cast<const void *>(k_fft_pass<true>), 227 * 1024);
     ensure_smem_attr(reinterpret_cast<const void *>(k_pointmul_mt), 65536);
     num_sms();
 }
@@ -760,7 +831,10 @@ static int resident_ctas(int threads, size_t smem) {
 int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, uint64_t P,
                     const uint4 *FA, const DevTables *T, int *status, cudaStream_t s, int count,
                     uint64_t strideF, uint64_t strideW, const uint4 *Fsrc, uint64_t strideFA) {
-    ensure_smem_attr(reinterpret_cast<const void *>(k_fft_pass), 227 * 1024);
+    const bool strided = p.c > 0;
+    ensure_smem_attr(strided ? reinterpret_cast<const void *>(k_fft_pass<true>)
+                             : reinterpret_cast<const void *>(k_fft_pass<false>),
+                     227 * 1024);
     FftPassArgs a;
     a.F = F;
     a.Fsrc = Fsrc;
@@ -794,7 +868,11 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
     int per_sm = resident_ctas(threads, smem);
     if (per_sm == 1) threads = std::max(threads, std::min(512, (1 << (p.g + p.c)) / 2));
     const uint64_t ctas = (uint64_t)num_sms() * per_sm;
-    k_fft_pass<<<(unsigned)std::min<uint64_t>(tiles, ctas), threads, smem, s>>>(a);
+    const unsigned grid = (unsigned)std::min<uint64_t>(tiles, ctas);
+    if (strided)
+        k_fft_pass<true><<<grid, threads, smem, s>>>(a);
+    else
+        k_fft_pass<false><<<grid, threads, smem, s>>>(a);
     return 0;
 }
 

@@ -8,7 +8,8 @@
 //    limb x is the XOR of seven shuffles indexed by its 5-bit windows (the
 //    lane index of a shuffle is taken modulo 32).  This is the method of four
 //    Russians of Sec. 4.3/4.4 with the table spread over the warp's registers
-//    instead of a cache.
+//    instead of a cache.  A variant takes the 2-bit window on the integer
+//    pipe (six shuffles per limb).
 //
 //  * The full F~_{2^8} product table (64 KiB in shared memory), when c differs
 //    from lane to lane: the F~_{2^32} product is Karatsuba over F~_{2^16} and
@@ -39,6 +40,69 @@ __device__ __forceinline__ uint32_t shfl_mul32(uint32_t x, const ShflTab &T) {
 __device__ __forceinline__ uint4 shfl_mul128(uint4 v, const ShflTab &T) {
     return make_uint4(shfl_mul32(v.x, T), shfl_mul32(v.y, T), shfl_mul32(v.z, T),
                       shfl_mul32(v.w, T));
+}
+
+// The same product with six shuffles per limb: the 2-bit window (bits 30, 31)
+// goes through the integer pipe instead, as x_30 c 2^30 + x_31 c 2^31 with the
+// two warp-uniform products c1 = c * 2^30, c2 = c * 2^31 masked by the bits.
+// The FFT passes run on the shuffle / shared-memory pipe; this moves a
+// seventh of their shuffles onto the integer ALU, which has room.
+struct ShflTab6 {
+    uint32_t t[6];
+    uint32_t c1, c2;
+};
+
+__device__ __forceinline__ uint32_t shfl6_mul32(uint32_t x, const ShflTab6 &T) {
+    uint32_t r = __shfl_sync(kFull, T.t[0], x);
+    r ^= __shfl_sync(kFull, T.t[1], x >> 5);
+    r ^= __shfl_sync(kFull, T.t[2], x >> 10);
+    r ^= __shfl_sync(kFull, T.t[3], x >> 15);
+    r ^= __shfl_sync(kFull, T.t[4], x >> 20);
+    r ^= __shfl_sync(kFull, T.t[5], x >> 25);
+    const uint32_t m31 = (uint32_t)((int32_t)x >> 31);         // all ones iff bit 31
+    const uint32_t m30 = (uint32_t)((int32_t)(x << 1) >> 31);  // all ones iff bit 30
+    return r ^ (m30 & T.c1) ^ (m31 & T.c2);
+}
+
+__device__ __forceinline__ uint4 shfl6_mul128(uint4 v, const ShflTab6 &T) {
+    return make_uint4(shfl6_mul32(v.x, T), shfl6_mul32(v.y, T), shfl6_mul32(v.z, T),
+                      shfl6_mul32(v.w, T));
+}
+
+// The six-shuffle table of c1 + c2 (so of the sum of two multipliers) from two
+// seven-word tables laid out [w][32 lanes]: words 0..5 at the calling lane of
+// each, and the two constants from lanes 2 and 3 of word 6 (c * 2^31 and
+// c * (2^30 + 2^31)), read as one 8-byte broadcast per table.  `a` may be in
+// shared or global memory, `b` is read through the read-only path.
+__device__ __forceinline__ ShflTab6 shfl6_table_sum(const uint32_t *a, const uint32_t *__restrict__ b,
+                                                    int lane) {
+    ShflTab6 T;
+#pragma unroll
+    for (int w = 0; w < 6; w++) T.t[w] = a[32 * w + lane] ^ __ldg(b + 32 * w + lane);
+    const uint2 pa = *reinterpret_cast<const uint2 *>(a + 6 * 32 + 2);
+    const uint2 pb = __ldg(reinterpret_cast<const uint2 *>(b + 6 * 32 + 2));
+    T.c2 = pa.x ^ pb.x;
+    T.c1 = pa.y ^ pb.y ^ T.c2;
+    return T;
+}
+
+// One seven-word table read the same way (global memory, read-only path).
+__device__ __forceinline__ ShflTab6 shfl6_table(const uint32_t *__restrict__ b, int lane) {
+    ShflTab6 T;
+#pragma unroll
+    for (int w = 0; w < 6; w++) T.t[w] = __ldg(b + 32 * w + lane);
+    const uint2 pb = __ldg(reinterpret_cast<const uint2 *>(b + 6 * 32 + 2));
+    T.c2 = pb.x;
+    T.c1 = pb.y ^ pb.x;
+    return T;
+}
+
+// The table of a sum of multipliers is the XOR of their tables.
+__device__ __forceinline__ void shfl6_xor(ShflTab6 &T, const ShflTab6 &U) {
+#pragma unroll
+    for (int w = 0; w < 6; w++) T.t[w] ^= U.t[w];
+    T.c1 ^= U.c1;
+    T.c2 ^= U.c2;
 }
 
 // ---- F~_{2^8} product table: mt[(c << 8) | x] = c * x ----------------------

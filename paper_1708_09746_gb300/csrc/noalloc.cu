@@ -125,11 +125,14 @@ int setup_current_device() {
             size_t nv, ns;
             pass_tables_size(g, uf, &nv, &ns);
             if (off + nv + ns > kPassWords) return false;
+            // both arrays start on 16-byte boundaries (the passes read two
+            // words of each shuffle table as one 8-byte load)
+            const size_t shfl = (off + nv + 3) & ~(size_t)3;
+            if (shfl + ns > kPassWords) return false;
             o->val = off;
-            o->shfl = off + nv;
+            o->shfl = shfl;
             pass_tables_fill(k_lo, g, uf, g_host_pass_words + o->val, g_host_pass_words + o->shfl);
-            off += nv + ns;
-            off = (off + 3) & ~(size_t)3;  // 16-byte aligned table starts
+            off = (shfl + ns + 3) & ~(size_t)3;
             return true;
         };
         for (int g = 0; g < kLocalSets; g++)
