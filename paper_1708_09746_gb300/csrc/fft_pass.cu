@@ -46,6 +46,7 @@
 #include "gf2x_internal.h"
 #include "gf2x_mul.cuh"
 #include "kernels.h"
+#include "launch.h"
 #include "tma.cuh"
 
 namespace gf2x {
@@ -396,6 +397,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     // seven in the strided ones (measured: the strided passes wait on their
     // table loads, not on the shuffle pipe, and lose with the longer chain)
     constexpr bool SIX = STRIDED ? kShfl6Strided : kShfl6Bottom;
+    pdl_release();
     extern __shared__ __align__(128) unsigned char smem[];
     const int g = a.g, c = a.c, uf = a.uf;
     // shuffle tables of the tile's multipliers for rows tb .. g-1 (all rows
@@ -458,11 +460,12 @@ __global__ void __launch_bounds__(512, 1) k_fft_pass(FftPassArgs a) {
     if ((int)threadIdx.x < g && blockIdx.x < ntiles)
         cnext[threadIdx.x] = tile_cval(a, blockIdx.x & tmask, threadIdx.x);
     __syncthreads();
-    if (blockIdx.x < ntiles) {
-        prefetch_tables(a, tb, cnext, stab);
-        if (warp == 0 && pipe)
-            tile_load_issue(G, src_of(blockIdx.x), src_tile(blockIdx.x & tmask), buf0, &bar[0], lane);
-    }
+    if (blockIdx.x < ntiles) prefetch_tables(a, tb, cnext, stab);
+    // everything above reads constant tables only; the tiles come from the
+    // previous kernels of the stream
+    pdl_acquire();
+    if (blockIdx.x < ntiles && warp == 0 && pipe)
+        tile_load_issue(G, src_of(blockIdx.x), src_tile(blockIdx.x & tmask), buf0, &bar[0], lane);
 
     bool aborted = false, prefetched = false;
     uint32_t i = 0;
@@ -869,10 +872,7 @@ int launch_fft_pass(const FftPassCfg &p, int M, uint4 *F, const uint64_t *g64, u
     if (per_sm == 1) threads = std::max(threads, std::min(512, (1 << (p.g + p.c)) / 2));
     const uint64_t ctas = (uint64_t)num_sms() * per_sm;
     const unsigned grid = (unsigned)std::min<uint64_t>(tiles, ctas);
-    if (strided)
-        k_fft_pass<true><<<grid, threads, smem, s>>>(a);
-    else
-        k_fft_pass<false><<<grid, threads, smem, s>>>(a);
+    launch_k(strided ? k_fft_pass<true> : k_fft_pass<false>, grid, threads, smem, s, a);
     return 0;
 }
 

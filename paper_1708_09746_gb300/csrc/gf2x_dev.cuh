@@ -39,6 +39,18 @@ struct DevTables {
 
 constexpr int kLowOff[3] = {0, 64, 96};
 
+// Programmatic dependent launch (kernels launched by launch_k): pdl_release
+// lets the next kernel of the stream be scheduled once every CTA of this one
+// has started; pdl_acquire returns once the earlier kernels of the stream have
+// completed and their writes are visible.  A kernel reads and writes nothing
+// that an earlier kernel of the stream touches before its pdl_acquire (only
+// constant tables are read before it).  Both are no-ops in a kernel launched
+// without the attribute.
+__device__ __forceinline__ void pdl_release() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_acquire() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) {
     return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
 }

@@ -4,6 +4,7 @@
 // batch costs one launch per kernel (blockIdx.y = product).
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <set>
@@ -13,8 +14,17 @@
 #include "gf2x_dev.cuh"
 #include "gf2x_internal.h"
 #include "kernels.h"
+#include "launch.h"
 
 namespace gf2x {
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("GF2X_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
 
 // ---------------------------------------------------------------------------
 // Split (Sec. 2.1): copy the operand's words, clear bits past its length and
@@ -22,6 +32,8 @@ namespace gf2x {
 // and writes w + y * stride.
 __global__ void k_split_pad(OperandDesc one, const OperandDesc *__restrict__ many,
                             uint64_t *__restrict__ w, uint64_t P, uint64_t stride) {
+    pdl_release();
+    pdl_acquire();
     const OperandDesc d = many ? many[blockIdx.y] : one;
     w += blockIdx.y * stride;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < P;
@@ -68,6 +80,8 @@ __device__ __forceinline__ void bcvt_item(T *f, uint64_t base, uint64_t E, uint6
 template <typename T>
 __global__ void k_bcvt_level(T *f, uint64_t n_half, int logE, int loge, int inverse,
                              uint64_t stride) {
+    pdl_release();
+    pdl_acquire();
     f += blockIdx.y * stride;
     const uint64_t E = 1ull << logE, e = 1ull << loge;
     for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < n_half;
@@ -216,6 +230,8 @@ static bool bcvt_tile_run_ok(int K, int G) {
 template <typename T, int G, int RM, bool INV, bool BND>
 __global__ void __launch_bounds__(256) k_bcvt_class(T *f, int a_top, int K, uint64_t n_el,
                                                     uint64_t stride) {
+    pdl_release();
+    pdl_acquire();
     constexpr int L = sizeof(T) / 4;
     f += blockIdx.y * stride;
     uint32_t *const F = reinterpret_cast<uint32_t *>(f);
@@ -363,6 +379,8 @@ __global__ void __launch_bounds__(SMALL ? 256 : 512,
                                   SMALL ? (sizeof(T) == 8 ? 4 : GF2X_BCVT128_MINB) : 1)
     k_bcvt_tile(T *f, int c, int lo, int w, LevelBatch lb,
                                                       int inverse, uint64_t stride) {
+    pdl_release();
+    pdl_acquire();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s = reinterpret_cast<T *>(smem_raw);
     f += blockIdx.y * stride;
@@ -430,6 +448,8 @@ __host__ __device__ constexpr uint32_t top_boundary(int h) { return (1u << h) + 
 template <typename T, int HR>
 __global__ void __launch_bounds__(kTopThreads) k_bcvt_top(T *f, int h, int inverse,
                                                           uint32_t n_bnd_ctas, uint64_t stride) {
+    pdl_release();
+    pdl_acquire();
     f += blockIdx.y * stride;
     const uint32_t B = top_boundary(h);
     if (blockIdx.x < n_bnd_ctas) {
@@ -536,11 +556,13 @@ __global__ void __launch_bounds__(256, 2) k_chrepr_stage(const uint64_t *__restr
                                                       uint64_t strideW, uint4 *__restrict__ F,
                                                       uint64_t strideF,
                                                       const DevTables *__restrict__ T) {
+    pdl_release();
     __shared__ __align__(16) uint32_t tab[4 * 2 * 7 * 32];
     const uint4 *src = reinterpret_cast<const uint4 *>(&T->phi_shfl[0][0][0][0]);
     for (int i = threadIdx.x; i < 4 * 2 * 7 * 32 / 4; i += blockDim.x)
         reinterpret_cast<uint4 *>(tab)[i] = __ldg(src + i);
     __syncthreads();
+    pdl_acquire();
     g += blockIdx.y * strideW;
     F += blockIdx.y * strideF;
     const int lane = threadIdx.x & 31;
@@ -605,11 +627,13 @@ __global__ void __launch_bounds__(256, 2) k_ichrepr_combine(const uint4 *__restr
                                                          const DevTables *__restrict__ T,
                                                          uint64_t j_begin, uint64_t j_end,
                                                          int accumulate) {
+    pdl_release();
     __shared__ __align__(16) uint32_t tab[4 * 4 * 7 * 32];
     const uint4 *src = reinterpret_cast<const uint4 *>(&T->psi_shfl[0][0][0][0]);
     for (int i = threadIdx.x; i < 4 * 4 * 7 * 32 / 4; i += blockDim.x)
         reinterpret_cast<uint4 *>(tab)[i] = __ldg(src + i);
     __syncthreads();
+    pdl_acquire();
     const OutputDesc d = many ? many[blockIdx.y] : one;
     F += blockIdx.y * stride;
     const int lane = threadIdx.x & 31;
@@ -721,7 +745,7 @@ static inline unsigned grid_for(uint64_t work, unsigned block, int count = 1) {
 void launch_split_pad(const OperandDesc &one, const OperandDesc *many, int count, uint64_t *w,
                       uint64_t P, uint64_t stride, cudaStream_t s) {
     dim3 grid(grid_for(P, 256, count), count);
-    k_split_pad<<<grid, 256, 0, s>>>(one, many, w, P, stride);
+    launch_k(k_split_pad, grid, 256, 0, s, one, many, w, P, stride);
 }
 
 // Tiles of 128 KiB: 2^14 words or 2^13 128-bit elements; rows of at least
@@ -757,12 +781,12 @@ static void launch_bcvt_top(T *f, int h, int inverse, cudaStream_t s, int count,
     const dim3 grid(nb + ni, count);
     const size_t smem = (size_t)kTopBoundaryClasses * ((1u << h) + 1) * sizeof(T);
     switch (HR) {
-        case 1: k_bcvt_top<T, 1><<<grid, kTopThreads, smem, s>>>(f, h, inverse, nb, stride); break;
-        case 2: k_bcvt_top<T, 2><<<grid, kTopThreads, smem, s>>>(f, h, inverse, nb, stride); break;
-        case 3: k_bcvt_top<T, 3><<<grid, kTopThreads, smem, s>>>(f, h, inverse, nb, stride); break;
-        case 4: k_bcvt_top<T, 4><<<grid, kTopThreads, smem, s>>>(f, h, inverse, nb, stride); break;
-        case 5: k_bcvt_top<T, 5><<<grid, kTopThreads, smem, s>>>(f, h, inverse, nb, stride); break;
-        default: k_bcvt_top<T, 6><<<grid, kTopThreads, smem, s>>>(f, h, inverse, nb, stride); break;
+        case 1: launch_k(k_bcvt_top<T, 1>, grid, kTopThreads, smem, s, f, h, inverse, nb, stride); break;
+        case 2: launch_k(k_bcvt_top<T, 2>, grid, kTopThreads, smem, s, f, h, inverse, nb, stride); break;
+        case 3: launch_k(k_bcvt_top<T, 3>, grid, kTopThreads, smem, s, f, h, inverse, nb, stride); break;
+        case 4: launch_k(k_bcvt_top<T, 4>, grid, kTopThreads, smem, s, f, h, inverse, nb, stride); break;
+        case 5: launch_k(k_bcvt_top<T, 5>, grid, kTopThreads, smem, s, f, h, inverse, nb, stride); break;
+        default: launch_k(k_bcvt_top<T, 6>, grid, kTopThreads, smem, s, f, h, inverse, nb, stride); break;
     }
 }
 
@@ -842,10 +866,10 @@ static void launch_bcvt_class(T *f, int m, const BcvtOp &o, int inverse, cudaStr
     const dim3 gb(grid_for(segs * r_int * L, 256, count), count);
 #define GF2X_CLASS_LAUNCH(GG, INV)                                                              \
     {                                                                                           \
-        k_bcvt_class<T, GG, (1 << GG) + 1, INV, false><<<gi, 256, 0, s>>>(f, o.a_top, o.K, n,  \
-                                                                          stride);              \
-        k_bcvt_class<T, GG, (1 << GG) + 1, INV, true><<<gb, 256, 0, s>>>(f, o.a_top, o.K, n,   \
-                                                                         stride);               \
+        launch_k(k_bcvt_class<T, GG, (1 << GG) + 1, INV, false>, gi, 256, 0, s, f, (int)o.a_top, \
+                 (int)o.K, n, stride);                                                          \
+        launch_k(k_bcvt_class<T, GG, (1 << GG) + 1, INV, true>, gb, 256, 0, s, f, (int)o.a_top,  \
+                 (int)o.K, n, stride);                                                          \
     }
     switch (o.G * 2 + (inverse ? 1 : 0)) {
         case 2: GF2X_CLASS_LAUNCH(1, false) break;
@@ -910,7 +934,7 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
         for (int q = 0; q < fwd.n; q++) {
             const Level &L = fwd.v[inverse ? fwd.n - 1 - q : q];
             dim3 grid(grid_for(n / 2, 256, count), count);
-            k_bcvt_level<T><<<grid, 256, 0, s>>>(f, n / 2, L.logE, L.loge, inverse, stride);
+            launch_k(k_bcvt_level<T>, grid, 256, 0, s, f, n / 2, (int)L.logE, (int)L.loge, inverse, stride);
             launches++;
         }
         return launches;
@@ -936,7 +960,7 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
             for (int t = 0; t < k; t++) {
                 const Level &L = lv[inverse ? k - 1 - t : t];
                 dim3 grid(grid_for(n / 2, 256, count), count);
-                k_bcvt_level<T><<<grid, 256, 0, s>>>(f, n / 2, L.logE, L.loge, inverse, stride);
+                launch_k(k_bcvt_level<T>, grid, 256, 0, s, f, n / 2, (int)L.logE, (int)L.loge, inverse, stride);
                 launches++;
             }
             i++;
@@ -976,9 +1000,9 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
         int threads = std::max(32, std::min(smem > 65536 ? 512 : small, 1 << (c + w - 1)));
         dim3 grid((unsigned)(n >> (c + w)), count);
         if (threads <= 256 && smem <= 65536)
-            k_bcvt_tile<T, true><<<grid, threads, smem, s>>>(f, c, lo, w, lb, inverse, stride);
+            launch_k(k_bcvt_tile<T, true>, grid, threads, smem, s, f, c, lo, w, lb, inverse, stride);
         else
-            k_bcvt_tile<T, false><<<grid, threads, smem, s>>>(f, c, lo, w, lb, inverse, stride);
+            launch_k(k_bcvt_tile<T, false>, grid, threads, smem, s, f, c, lo, w, lb, inverse, stride);
         launches++;
         i = j;
     }
@@ -1010,7 +1034,7 @@ void launch_chrepr_stage(const uint64_t *g, uint64_t P, uint64_t strideW, uint4 
     const uint64_t per = std::max<uint64_t>(1, (uint64_t)num_sms() * 4 / (uint64_t)std::max(count, 1));
     const uint64_t need = (P + 8 * 32 * kChreprK - 1) / (8 * 32 * kChreprK);
     dim3 grid((unsigned)std::max<uint64_t>(1, std::min<uint64_t>(need, per)), count);
-    k_chrepr_stage<<<grid, 256, 0, s>>>(g, P, strideW, F, strideF, T);
+    launch_k(k_chrepr_stage, grid, 256, 0, s, g, P, strideW, F, strideF, T);
 }
 
 void launch_chrepr(const uint64_t *g, uint64_t P, uint4 *F, uint64_t n, const DevTables *T,
@@ -1028,8 +1052,8 @@ void launch_ichrepr_combine(const uint4 *F, uint64_t n, uint64_t stride, const O
     const uint64_t span = std::min(j_end, max_words) > j_begin ? std::min(j_end, max_words) - j_begin : 0;
     const uint64_t need = (span + 8 * (32 * kCombineK - 1) - 1) / (8 * (32 * kCombineK - 1));
     dim3 grid((unsigned)std::max<uint64_t>(1, std::min(need, per)), count);
-    k_ichrepr_combine<<<grid, 256, 0, s>>>(F, n, stride, one, many, T, j_begin, j_end,
-                                           accumulate ? 1 : 0);
+    launch_k(k_ichrepr_combine, grid, 256, 0, s, F, n, stride, one, many, T, j_begin, j_end,
+             accumulate ? 1 : 0);
 }
 
 __global__ void k_chunk_descs(const uint64_t *x, uint64_t xw, uint64_t x_mask, uint64_t L,

@@ -14,7 +14,9 @@
 #include <algorithm>
 
 #include "clmul.cuh"
+#include "gf2x_dev.cuh"
 #include "kernels.h"
+#include "launch.h"
 #include "small.h"
 
 namespace gf2x {
@@ -31,6 +33,8 @@ __global__ void __launch_bounds__(256) k_mul_small(const uint64_t *__restrict__ 
                                                    int yw, uint64_t y_mask, uint64_t *out,
                                                    uint64_t nprod, uint64_t out_limit, uint64_t off,
                                                    int accumulate) {
+    pdl_release();
+    pdl_acquire();
     __shared__ uint64_t ys[kSmallWords];
     if ((int)threadIdx.x < yw) {
         uint64_t v = y[threadIdx.x];
@@ -134,8 +138,8 @@ void launch_mul_small(const uint64_t *x, uint64_t x_bits, const uint64_t *y, uin
     const uint64_t threads = (nprod + kWordsPerThread - 1) / kWordsPerThread;
     const unsigned grid = (unsigned)std::max<uint64_t>(
         1, std::min<uint64_t>((threads + 255) / 256, (uint64_t)num_sms() * 16));
-    k_mul_small<<<grid, 256, 0, s>>>(x, xw, mx, y, (int)yw, my, out, nprod, out_limit, off,
-                                     accumulate ? 1 : 0);
+    launch_k(k_mul_small, grid, 256, 0, s, x, xw, mx, y, (int)yw, my, out, nprod, out_limit, off,
+             accumulate ? 1 : 0);
 }
 
 bool tail_split(uint64_t aw, uint64_t bw, uint64_t *A, uint64_t *B) {
