@@ -374,17 +374,83 @@ __device__ __forceinline__ void bcvt_op(T *s, uint32_t tile, const BcvtOp &op) {
 #ifndef GF2X_BCVT128_MINB
 #define GF2X_BCVT128_MINB 3
 #endif
-template <typename T, bool SMALL>
+//
+// PHI (64-bit blocks, the last pass of a forward conversion): the tile leaves
+// as changeRepr'd 128-bit elements (tile_store_phi) to phi.out and f is not
+// written; three CTAs per SM (80 registers, no spills; at 64 registers the
+// store's tables spill).
+constexpr int kPhiTabWords = 4 * 2 * 7 * 32;  // DevTables::phi_shfl
+
+// changeRepr of a tile's blocks on the way out: word o of phi(b) is the XOR of
+// the 14 five-bit-window entries of b's two 32-bit halves (DevTables::phi_shfl,
+// staged in shared memory; lane l holds entry l of a window's table and a
+// lookup is one shuffle).  A warp takes 128 consecutive tile entries (lane l:
+// entries l + 32 k), one output word of phi at a time, and writes each
+// element at its global index.
+__device__ __forceinline__ void tile_store_phi(const uint64_t *s, uint32_t tile, uint4 *out,
+                                               uint64_t base, int c, int lo, const uint32_t *tab) {
+    constexpr int K = 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t cmask = (1u << c) - 1;
+    for (uint32_t c0 = warp * 32u * K; c0 < tile; c0 += nw * 32u * K) {
+        uint32_t b[K][2];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint32_t i = c0 + 32 * k + lane;
+            const uint64_t v = i < tile ? s[sw(i)] : 0;
+            b[k][0] = (uint32_t)v;
+            b[k][1] = (uint32_t)(v >> 32);
+        }
+        uint32_t r[K][4] = {};
+#pragma unroll 1
+        for (int o = 0; o < 4; o++) {
+            uint32_t tb[14];
+#pragma unroll
+            for (int qw = 0; qw < 14; qw++) tb[qw] = tab[(o * 14 + qw) * 32 + lane];
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                uint32_t wv[2] = {b[k][0], b[k][1]};
+                asm volatile("" : "+r"(wv[0]), "+r"(wv[1]));  // shifts stay inside the loop over o
+                uint32_t acc = 0;
+#pragma unroll
+                for (int q = 0; q < 2; q++) {
+#pragma unroll
+                    for (int wd = 0; wd < 6; wd++)
+                        acc ^= __shfl_sync(0xffffffffu, tb[q * 7 + wd], wv[q] >> (5 * wd));
+                    acc ^= __shfl_sync(0xffffffffu, tb[q * 7 + 6], wv[q] >> 30);
+                }
+#pragma unroll
+                for (int oo = 0; oo < 4; oo++) r[k][oo] = o == oo ? acc : r[k][oo];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint32_t i = c0 + 32 * k + lane;
+            if (i < tile)
+                out[base | ((uint64_t)(i >> c) << lo) | (i & cmask)] =
+                    make_uint4(r[k][0], r[k][1], r[k][2], r[k][3]);
+        }
+    }
+}
+
+template <typename T, bool SMALL, bool PHI>
 __global__ void __launch_bounds__(SMALL ? 256 : 512,
-                                  SMALL ? (sizeof(T) == 8 ? 4 : GF2X_BCVT128_MINB) : 1)
+                                  SMALL ? (sizeof(T) == 8 ? (PHI ? 3 : 4) : GF2X_BCVT128_MINB) : 1)
     k_bcvt_tile(T *f, int c, int lo, int w, LevelBatch lb,
-                                                      int inverse, uint64_t stride) {
+                                                      int inverse, uint64_t stride, PhiOut phi) {
+    static_assert(!PHI || sizeof(T) == 8, "changeRepr applies to 64-bit blocks");
     pdl_release();
-    pdl_acquire();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s = reinterpret_cast<T *>(smem_raw);
-    f += blockIdx.y * stride;
     const uint32_t tile = 1u << (c + w);
+    uint32_t *phi_tab = reinterpret_cast<uint32_t *>(smem_raw + sizeof(T) * (size_t)tile);
+    if (PHI) {  // constant tables: before the wait
+        const uint4 *src = reinterpret_cast<const uint4 *>(&phi.T->phi_shfl[0][0][0][0]);
+        for (int i = threadIdx.x; i < kPhiTabWords / 4; i += blockDim.x)
+            reinterpret_cast<uint4 *>(phi_tab)[i] = __ldg(src + i);
+    }
+    pdl_acquire();
+    f += blockIdx.y * stride;
     const int mid_bits = lo - c;
     const uint64_t mid = blockIdx.x & ((1ull << mid_bits) - 1);
     const uint64_t hi = (uint64_t)blockIdx.x >> mid_bits;
@@ -412,6 +478,10 @@ __global__ void __launch_bounds__(SMALL ? 256 : 512,
         else
             bcvt_op<T, false>(s, tile, lb.op[L]);
         __syncthreads();
+    }
+    if constexpr (PHI) {
+        tile_store_phi(s, tile, phi.out + blockIdx.y * phi.stride, base, c, lo, phi_tab);
+        return;
     }
     for (uint32_t i = threadIdx.x; i < tile; i += blockDim.x)
         f[base | ((uint64_t)(i >> c) << lo) | (i & cmask)] = s[sw(i)];
@@ -892,10 +962,17 @@ static void launch_bcvt_class(T *f, int m, const BcvtOp &o, int inverse, cudaStr
 // list `fwd` (the divisions of Alg. 3 in order) before anything is launched.
 template <typename T>
 uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStream_t s, int count,
-                       uint64_t stride, const BcvtTune &tune) {
-    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<T, false>),
+                       uint64_t stride, const BcvtTune &tune, const PhiOut *phi, bool *phi_done) {
+    if (phi_done) *phi_done = false;
+    const bool want_phi = sizeof(T) == 8 && !inverse && phi && phi->out && phi->T;
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<T, false, false>),
                      (int)(sizeof(T) << tile_log_for<T>()));
-    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<T, true>), 65536);
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<T, true, false>), 65536);
+    if constexpr (sizeof(T) == 8) {
+        ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<T, false, true>),
+                         (int)((sizeof(T) << tile_log_for<T>()) + 4 * kPhiTabWords));
+        ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<T, true, true>), 65536);
+    }
     uint64_t launches = 0;
     const int h_top = top_levels(m, fwd);
     const int budget = std::min(tile_log_for<T>(), m), cmin = min_cols_for<T>();
@@ -995,14 +1072,30 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
             o.a_top = (int8_t)(o.a_top - lo + c);  // tile-local index bits
             lb.op[q - i] = o;
         }
+        // the last pass of a forward conversion (the top VarSubs comes first)
+        // writes the changeRepr'd elements when asked to
+        PhiOut po;
+        if (want_phi && j == ops.n) {
+            po = *phi;
+            if (phi_done) *phi_done = true;
+        }
         size_t smem = sizeof(T) << (c + w);
         const int small = std::max(32, std::min(512, tune.small_threads));
         int threads = std::max(32, std::min(smem > 65536 ? 512 : small, 1 << (c + w - 1)));
+        if (po.out) smem += 4 * kPhiTabWords;
         dim3 grid((unsigned)(n >> (c + w)), count);
-        if (threads <= 256 && smem <= 65536)
-            launch_k(k_bcvt_tile<T, true>, grid, threads, smem, s, f, c, lo, w, lb, inverse, stride);
-        else
-            launch_k(k_bcvt_tile<T, false>, grid, threads, smem, s, f, c, lo, w, lb, inverse, stride);
+        const bool sm = threads <= 256 && smem <= 65536;
+        if constexpr (sizeof(T) == 8) {
+            if (po.out) {
+                launch_k(sm ? k_bcvt_tile<T, true, true> : k_bcvt_tile<T, false, true>, grid,
+                         threads, smem, s, f, c, lo, w, lb, inverse, stride, po);
+                launches++;
+                i = j;
+                continue;
+            }
+        }
+        launch_k(sm ? k_bcvt_tile<T, true, false> : k_bcvt_tile<T, false, false>, grid, threads,
+                 smem, s, f, c, lo, w, lb, inverse, stride, po);
         launches++;
         i = j;
     }
@@ -1014,19 +1107,22 @@ uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStrea
 }
 
 void prepare_bcvt_attributes() {
-    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint64_t, false>),
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint64_t, false, false>),
                      (int)(sizeof(uint64_t) << tile_log_for<uint64_t>()));
-    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint4, false>),
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint64_t, false, true>),
+                     (int)((sizeof(uint64_t) << tile_log_for<uint64_t>()) + 4 * kPhiTabWords));
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint4, false, false>),
                      (int)(sizeof(uint4) << tile_log_for<uint4>()));
-    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint64_t, true>), 65536);
-    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint4, true>), 65536);
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint64_t, true, false>), 65536);
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint64_t, true, true>), 65536);
+    ensure_smem_attr(reinterpret_cast<const void *>(k_bcvt_tile<uint4, true, false>), 65536);
     num_sms();
 }
 
 template uint64_t run_basis_cvt<uint64_t>(uint64_t *, int, const LevelList &, int, cudaStream_t,
-                                          int, uint64_t, const BcvtTune &);
+                                          int, uint64_t, const BcvtTune &, const PhiOut *, bool *);
 template uint64_t run_basis_cvt<uint4>(uint4 *, int, const LevelList &, int, cudaStream_t, int,
-                                       uint64_t, const BcvtTune &);
+                                       uint64_t, const BcvtTune &, const PhiOut *, bool *);
 
 void launch_chrepr_stage(const uint64_t *g, uint64_t P, uint64_t strideW, uint4 *F,
                          uint64_t strideF, int count, const DevTables *T, cudaStream_t s) {

@@ -68,9 +68,23 @@ struct BcvtTune {
     int small_threads = 256;
 };
 
+// changeRepr fused into the last tile pass of a forward BasisCvt of 64-bit
+// blocks: that pass writes phi(block) as a 128-bit element to out + y * stride
+// (the staged blocks the first strided FFT pass reads) instead of the block
+// back in place.
+struct PhiOut {
+    uint4 *out = nullptr;
+    uint64_t stride = 0;
+    const DevTables *T = nullptr;
+};
+
+// `phi` (forward, 64-bit blocks only): take changeRepr into the last pass if
+// that pass is a tile pass; *phi_done tells whether it was (else the blocks are
+// converted in place as usual and changeRepr remains to be done).
 template <typename T>
 uint64_t run_basis_cvt(T *f, int m, const LevelList &fwd, int inverse, cudaStream_t s,
-                       int count = 1, uint64_t stride = 0, const BcvtTune &tune = BcvtTune());
+                       int count = 1, uint64_t stride = 0, const BcvtTune &tune = BcvtTune(),
+                       const PhiOut *phi = nullptr, bool *phi_done = nullptr);
 
 // changeRepr of the P blocks of `count` operands (product y at g + y * strideW)
 // into F + y * strideF, ahead of their first strided FFT pass.

@@ -151,12 +151,16 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
     begin(ST_SPLIT);
     launch_split_pad(one_a, many_a, count, WA, p->Pa, sW, s);
     end(1);
-    begin(ST_BCVT);
-    end(run_basis_cvt<uint64_t>(WA, p->pa_log, p->lv_a, 0, s, count, sW, p->tune.bcvt));
     // with strided passes: changeRepr into ST, which the first pass reads
-    // periodically; a lone bottom pass reads the blocks and converts them itself
+    // periodically (done by the last BasisCvt tile pass where it is one); a
+    // lone bottom pass reads the blocks and converts them itself
     const bool st_a = p->fft_a.n > 1;
-    if (st_a) {
+    const PhiOut phi{ST, sF, T};
+    bool phi_done = false;
+    begin(ST_BCVT);
+    end(run_basis_cvt<uint64_t>(WA, p->pa_log, p->lv_a, 0, s, count, sW, p->tune.bcvt,
+                                st_a ? &phi : nullptr, &phi_done));
+    if (st_a && !phi_done) {
         begin(ST_CHREPR);
         launch_chrepr_stage(WA, p->Pa, sW, ST, sF, count, T, s);
         end(1);
@@ -172,8 +176,9 @@ int plan_run_batch(const gf2x_plan *p, int count, const OperandDesc *many_a,
     launch_split_pad(one_b, many_b, count, WB, p->Pb, sW, s);
     end(1);
     begin(ST_BCVT);
-    end(run_basis_cvt<uint64_t>(WB, p->pb_log, p->lv_b, 0, s, count, sW, p->tune.bcvt));
-    if (p->fft_b.n > 0) {
+    end(run_basis_cvt<uint64_t>(WB, p->pb_log, p->lv_b, 0, s, count, sW, p->tune.bcvt,
+                                p->fft_b.n > 0 ? &phi : nullptr, &phi_done));
+    if (p->fft_b.n > 0 && !phi_done) {
         begin(ST_CHREPR);
         launch_chrepr_stage(WB, p->Pb, sW, ST, sF, count, T, s);
         end(1);
