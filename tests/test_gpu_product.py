@@ -90,6 +90,49 @@ def test_bits_past_length_ignored():
     assert np.array_equal(gpu_mul(a_dirty, na, b_dirty, nb), P.mul(a, na, b, nb))
 
 
+def _dirty(x, n):
+    """x with every bit past its length n set in the last word (and one word
+    more), which the product must ignore."""
+    y = np.concatenate([x.copy(), np.array([~np.uint64(0)], dtype=np.uint64)])
+    if n % 64:
+        y[(n - 1) // 64] |= np.uint64(~((1 << (n % 64)) - 1) & (2**64 - 1))
+    return y
+
+
+# Operands of 2^17 words and more (their BasisCvt starts with the top VarSubs
+# pass), with every bit past their lengths set: Split must pad with zeros and
+# mask the last word; lengths past a power of two, 2^17- to 2^19-block
+# conversions
+SPLIT_LARGE = [((1 << 23) + 77, (1 << 23) - 5), ((1 << 24) + 1, (1 << 23) + 3),
+             ((1 << 23) + 64, (1 << 22) + 7)]
+
+
+@pytest.mark.parametrize("na,nb", SPLIT_LARGE)
+def test_split_large_dirty(na, nb):
+    a, b = W.operand_pair(na % 1009 + nb, na, nb)
+    got = gpu_mul(_dirty(a, na), na, _dirty(b, nb), nb)
+    assert np.array_equal(got, P.mul(a, na, b, nb))
+
+
+def test_split_large_dirty_batched():
+    # two products of one shape in one grouped launch: Split reads each
+    # product's operand through its descriptor
+    na, nb = (1 << 23) + 77, (1 << 23) - 5
+    prods = [W.operand_pair(300 + i, na, nb) for i in range(2)]
+    batch = G.gf2x_batch_create([na, na], [nb, nb], 1 << 30)
+    try:
+        da = [to_dev(_dirty(a, na)) for a, _ in prods]
+        db = [to_dev(_dirty(b, nb)) for _, b in prods]
+        outs = [empty_dev(G.gf2x_out_words(na, nb)) for _ in prods]
+        G.gf2x_batch_execute(batch, da, db, outs)
+        torch.cuda.synchronize()
+        for (a, b), o in zip(prods, outs):
+            want = P.mul(a, na, b, nb)
+            assert np.array_equal(from_dev(o, len(want)), want)
+    finally:
+        G.gf2x_batch_destroy(batch)
+
+
 def test_all_ones_and_sparse():
     n = 1 << 18
     o = W.all_ones(n)
