@@ -142,12 +142,81 @@ __device__ __forceinline__ void reg_subpass(uint4 *s, int c, int g, int r_lo, in
     }
 }
 
+// Two-row sub-pass of a strided tile (c >= 6) with two columns per thread, col
+// and col + 32: the columns share every multiplier, so each table read serves
+// both (eight elements in registers, as in a three-row sub-pass).  Pair p
+// takes the items q = 64 (p >> 5) + (p & 31) and q + 32; the 32 lanes of a warp
+// hold consecutive columns of one row group.
+#ifndef GF2X_STRIDED_PAIR
+#define GF2X_STRIDED_PAIR 1
+#endif
+template <bool INV>
+__device__ __forceinline__ void reg_subpass2_pair(uint4 *s, int c, int g, int r_lo, int uf,
+                                                  const uint32_t *ctab,
+                                                  const uint32_t *__restrict__ d_shfl) {
+    const int r_hi = r_lo + 1;
+    const uint32_t pairs = 1u << (g + c - 3);
+    const int lane = threadIdx.x & 31;
+    const uint32_t cmask = (1u << c) - 1, lomask = (1u << r_lo) - 1;
+    for (uint32_t p = threadIdx.x; p < pairs; p += blockDim.x) {
+        const uint32_t q = ((p >> 5) << 6) | (p & 31);
+        const uint32_t col = q & cmask, rest = q >> c;
+        const uint32_t lo_rows = rest & lomask, hi_rows = rest >> r_lo;
+        const uint32_t base_row = (hi_rows << (r_hi + 1)) | lo_rows;
+        uint4 e[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int m = 0; m < 4; m++)
+                e[h][m] = s[((base_row | ((uint32_t)m << r_lo)) << c) | (col | (uint32_t)(h << 5))];
+#pragma unroll
+        for (int step = 0; step < 2; step++) {
+            const int rr = INV ? step : 1 - step;
+            const int r = r_lo + rr;
+            const uint32_t off = (1u << (g - uf)) - (1u << (g - r));
+#pragma unroll
+            for (int B = 0; B < (2 >> rr); B++) {
+                const uint32_t prefix = (hi_rows << (r_hi - r)) | (uint32_t)B;
+                const uint32_t *ct = ctab + (r - uf) * 224;
+                const uint32_t *dt = d_shfl + (size_t)(off + prefix) * 224;
+                ShflTab T;
+#pragma unroll
+                for (int w = 0; w < 7; w++) T.t[w] = ct[32 * w + lane] ^ __ldg(dt + 32 * w + lane);
+#pragma unroll
+                for (int h = 0; h < 2; h++)
+#pragma unroll
+                    for (int j = 0; j < (1 << rr); j++) {
+                        uint4 &u = e[h][B * (2 << rr) + j];
+                        uint4 &v = e[h][B * (2 << rr) + j + (1 << rr)];
+                        if (!INV) {
+                            u = xor4(u, shfl_mul128(v, T));
+                            v = xor4(v, u);
+                        } else {
+                            v = xor4(v, u);
+                            u = xor4(u, shfl_mul128(v, T));
+                        }
+                    }
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int m = 0; m < 4; m++)
+                s[((base_row | ((uint32_t)m << r_lo)) << c) | (col | (uint32_t)(h << 5))] = e[h][m];
+    }
+}
+
 template <bool INV, bool SIX>
 __device__ __forceinline__ void run_subpass(int G, uint4 *s, int c, int g, int r_lo, int uf,
                                             const uint32_t *ctab, const uint32_t *d_shfl) {
     switch (G) {
         case 1: reg_subpass<1, INV, SIX>(s, c, g, r_lo, uf, ctab, d_shfl); break;
-        case 2: reg_subpass<2, INV, SIX>(s, c, g, r_lo, uf, ctab, d_shfl); break;
+        case 2:
+            if (GF2X_STRIDED_PAIR && !SIX && c >= 6)
+                reg_subpass2_pair<INV>(s, c, g, r_lo, uf, ctab, d_shfl);
+            else
+                reg_subpass<2, INV, SIX>(s, c, g, r_lo, uf, ctab, d_shfl);
+            break;
         case 3: reg_subpass<3, INV, SIX>(s, c, g, r_lo, uf, ctab, d_shfl); break;
         default: reg_subpass<3, INV, SIX>(s, c, g, r_lo, uf, ctab, d_shfl); break;
     }

@@ -685,11 +685,17 @@ __global__ void __launch_bounds__(256, 2) k_chrepr_stage(const uint64_t *__restr
 // output word.  psi is F_2-linear, so word o of psi(x) is the XOR over the 28
 // windows of x (seven per input word q, as in shfl_mul32) of the table entry
 // psi_shfl[o][q][w][window value]; lane l holds entry l of each window's table
-// in a register and a window lookup is one shuffle.  A warp takes chunks of
+// in a register and a window lookup is one shuffle (the six 5-bit windows of a
+// word; its 2-bit window as two masked XORs of warp-uniform entries).  A warp takes chunks of
 // 32 K consecutive elements (lane l: elements l, l + 32, ...) and writes the
 // 32 K - 1 output words that need only those elements; chunks overlap by one
 // element.
 constexpr int kCombineK = 8;
+// 1: the 2-bit window of every input word through the integer pipe (24
+// shuffles per output word instead of 28)
+#ifndef GF2X_PSI_SHFL6
+#define GF2X_PSI_SHFL6 1
+#endif
 
 __global__ void __launch_bounds__(256, 2) k_ichrepr_combine(const uint4 *__restrict__ F, uint64_t n,
                                                          uint64_t stride, OutputDesc one,
@@ -728,9 +734,23 @@ __global__ void __launch_bounds__(256, 2) k_ichrepr_combine(const uint4 *__restr
         uint32_t r[kCombineK][4];
 #pragma unroll 1
         for (int o = 0; o < 4; o++) {
+#if GF2X_PSI_SHFL6
+            // the 2-bit window of each input word on the integer pipe: its
+            // entries for 2^31 and 2^30 + 2^31 are lanes 2 and 3 of table w = 6
+            uint32_t tb[24], c1[4], c2[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+#pragma unroll
+                for (int w = 0; w < 6; w++) tb[q * 6 + w] = tab[(o * 28 + q * 7 + w) * 32 + lane];
+                const uint2 p = *reinterpret_cast<const uint2 *>(&tab[(o * 28 + q * 7 + 6) * 32 + 2]);
+                c2[q] = p.x;
+                c1[q] = p.x ^ p.y;
+            }
+#else
             uint32_t tb[28];
 #pragma unroll
             for (int qw = 0; qw < 28; qw++) tb[qw] = tab[(o * 28 + qw) * 32 + lane];
+#endif
 #pragma unroll
             for (int k = 0; k < kCombineK; k++) {
                 uint32_t wv[4] = {e[k].x, e[k].y, e[k].z, e[k].w};
@@ -741,9 +761,17 @@ __global__ void __launch_bounds__(256, 2) k_ichrepr_combine(const uint4 *__restr
                 uint32_t acc = 0;
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
+#if GF2X_PSI_SHFL6
+#pragma unroll
+                    for (int w = 0; w < 6; w++) acc ^= __shfl_sync(0xffffffffu, tb[q * 6 + w], wv[q] >> (5 * w));
+                    const uint32_t m31 = (uint32_t)((int32_t)wv[q] >> 31);
+                    const uint32_t m30 = (uint32_t)((int32_t)(wv[q] << 1) >> 31);
+                    acc ^= (m30 & c1[q]) ^ (m31 & c2[q]);
+#else
 #pragma unroll
                     for (int w = 0; w < 6; w++) acc ^= __shfl_sync(0xffffffffu, tb[q * 7 + w], wv[q] >> (5 * w));
                     acc ^= __shfl_sync(0xffffffffu, tb[q * 7 + 6], wv[q] >> 30);
+#endif
                 }
 #pragma unroll
                 for (int oo = 0; oo < 4; oo++) r[k][oo] = o == oo ? acc : r[k][oo];
