@@ -74,6 +74,11 @@ uint32_t wait_spins() { return g_wait_spins.load(); }
 constexpr bool kShfl6Strided = GF2X_SHFL6_STRIDED != 0;
 constexpr bool kShfl6Bottom = GF2X_SHFL6_BOTTOM != 0;
 
+#ifndef GF2X_STRIDED_OFFSET_ROW
+#define GF2X_STRIDED_OFFSET_ROW 1
+#endif
+constexpr bool kStridedOffsetRow = GF2X_STRIDED_OFFSET_ROW != 0;
+
 // ---------------------------------------------------------------------------
 // Register sub-pass: G layers (tile rows r_lo .. r_lo+G-1) on columns of 2^G
 // elements held by one thread.  Requires c + r_lo >= 5 so that a warp's lanes
@@ -86,6 +91,17 @@ __device__ __forceinline__ void reg_subpass(uint4 *s, int c, int g, int r_lo, in
     const uint32_t items = 1u << (g + c - G);
     const int lane = threadIdx.x & 31;
     const uint32_t cmask = (1u << c) - 1, lomask = (1u << r_lo) - 1;
+    // strided three-row sub-passes: the tables of d(k, 1), d(k, 2) of the lowest
+    // row, read once per call
+    ShflTab R1, R2, T0s;
+    if (!SIX && G == 3 && kStridedOffsetRow) {
+        const uint32_t off0 = (1u << (g - uf)) - (1u << (g - r_lo));
+#pragma unroll
+        for (int w = 0; w < 7; w++) {
+            R1.t[w] = __ldg(d_shfl + (size_t)(off0 + 1) * 224 + 32 * w + lane);
+            R2.t[w] = __ldg(d_shfl + (size_t)(off0 + 2) * 224 + 32 * w + lane);
+        }
+    }
     for (uint32_t q = threadIdx.x; q < items; q += blockDim.x) {
         const uint32_t col = q & cmask, rest = q >> c;
         const uint32_t lo_rows = rest & lomask, hi_rows = rest >> r_lo;
@@ -120,8 +136,19 @@ __device__ __forceinline__ void reg_subpass(uint4 *s, int c, int g, int r_lo, in
                     }
                 } else {
                     ShflTab T;
+                    if (G == 3 && rr == 0 && kStridedOffsetRow) {
+                        // block B's table = block 0's + the kept table of d(k, B)
+                        if (B == 0) {
 #pragma unroll
-                    for (int w = 0; w < 7; w++) T.t[w] = ct[32 * w + lane] ^ __ldg(dt + 32 * w + lane);
+                            for (int w = 0; w < 7; w++) T0s.t[w] = ct[32 * w + lane] ^ __ldg(dt + 32 * w + lane);
+                        }
+#pragma unroll
+                        for (int w = 0; w < 7; w++)
+                            T.t[w] = T0s.t[w] ^ ((B & 1) ? R1.t[w] : 0u) ^ ((B & 2) ? R2.t[w] : 0u);
+                    } else {
+#pragma unroll
+                        for (int w = 0; w < 7; w++) T.t[w] = ct[32 * w + lane] ^ __ldg(dt + 32 * w + lane);
+                    }
 #pragma unroll
                     for (int j = 0; j < (1 << rr); j++) {
                         uint4 &u = e[B * (2 << rr) + j];
