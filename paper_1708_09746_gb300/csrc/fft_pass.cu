@@ -74,10 +74,17 @@ uint32_t wait_spins() { return g_wait_spins.load(); }
 constexpr bool kShfl6Strided = GF2X_SHFL6_STRIDED != 0;
 constexpr bool kShfl6Bottom = GF2X_SHFL6_BOTTOM != 0;
 
-#ifndef GF2X_STRIDED_OFFSET_ROW
-#define GF2X_STRIDED_OFFSET_ROW 1
+// Rows (from the lowest) of a strided three-row sub-pass whose block tables are
+// block 0's plus kept offset tables; 1: also the lower row of a paired two-row
+// sub-pass.
+#ifndef GF2X_STRIDED_OFFSET_ROWS
+#define GF2X_STRIDED_OFFSET_ROWS 2
 #endif
-constexpr bool kStridedOffsetRow = GF2X_STRIDED_OFFSET_ROW != 0;
+#ifndef GF2X_PAIR_OFFSET
+#define GF2X_PAIR_OFFSET 0
+#endif
+constexpr int kStridedOffsetRows = GF2X_STRIDED_OFFSET_ROWS;
+constexpr bool kPairOffset = GF2X_PAIR_OFFSET != 0;
 
 // ---------------------------------------------------------------------------
 // Register sub-pass: G layers (tile rows r_lo .. r_lo+G-1) on columns of 2^G
@@ -93,13 +100,15 @@ __device__ __forceinline__ void reg_subpass(uint4 *s, int c, int g, int r_lo, in
     const uint32_t cmask = (1u << c) - 1, lomask = (1u << r_lo) - 1;
     // strided three-row sub-passes: the tables of d(k, 1), d(k, 2) of the lowest
     // row, read once per call
-    ShflTab R1, R2, T0s;
-    if (!SIX && G == 3 && kStridedOffsetRow) {
+    ShflTab R1, R2, R3, T0s;
+    if (!SIX && G == 3 && kStridedOffsetRows > 0) {
         const uint32_t off0 = (1u << (g - uf)) - (1u << (g - r_lo));
+        const uint32_t off1 = (1u << (g - uf)) - (1u << (g - r_lo - 1));
 #pragma unroll
         for (int w = 0; w < 7; w++) {
             R1.t[w] = __ldg(d_shfl + (size_t)(off0 + 1) * 224 + 32 * w + lane);
             R2.t[w] = __ldg(d_shfl + (size_t)(off0 + 2) * 224 + 32 * w + lane);
+            R3.t[w] = __ldg(d_shfl + (size_t)(off1 + 1) * 224 + 32 * w + lane);
         }
     }
     for (uint32_t q = threadIdx.x; q < items; q += blockDim.x) {
@@ -136,15 +145,20 @@ __device__ __forceinline__ void reg_subpass(uint4 *s, int c, int g, int r_lo, in
                     }
                 } else {
                     ShflTab T;
-                    if (G == 3 && rr == 0 && kStridedOffsetRow) {
+                    if (G == 3 && rr < kStridedOffsetRows) {
                         // block B's table = block 0's + the kept table of d(k, B)
                         if (B == 0) {
 #pragma unroll
                             for (int w = 0; w < 7; w++) T0s.t[w] = ct[32 * w + lane] ^ __ldg(dt + 32 * w + lane);
                         }
+                        if (rr == 0) {
 #pragma unroll
-                        for (int w = 0; w < 7; w++)
-                            T.t[w] = T0s.t[w] ^ ((B & 1) ? R1.t[w] : 0u) ^ ((B & 2) ? R2.t[w] : 0u);
+                            for (int w = 0; w < 7; w++)
+                                T.t[w] = T0s.t[w] ^ ((B & 1) ? R1.t[w] : 0u) ^ ((B & 2) ? R2.t[w] : 0u);
+                        } else {
+#pragma unroll
+                            for (int w = 0; w < 7; w++) T.t[w] = T0s.t[w] ^ ((B & 1) ? R3.t[w] : 0u);
+                        }
                     } else {
 #pragma unroll
                         for (int w = 0; w < 7; w++) T.t[w] = ct[32 * w + lane] ^ __ldg(dt + 32 * w + lane);
@@ -185,6 +199,13 @@ __device__ __forceinline__ void reg_subpass2_pair(uint4 *s, int c, int g, int r_
     const uint32_t pairs = 1u << (g + c - 3);
     const int lane = threadIdx.x & 31;
     const uint32_t cmask = (1u << c) - 1, lomask = (1u << r_lo) - 1;
+    // the lower row's block 1 table = block 0's + the kept table of d(k, 1)
+    ShflTab R1, T0;
+    if (kPairOffset) {
+        const uint32_t off0 = (1u << (g - uf)) - (1u << (g - r_lo));
+#pragma unroll
+        for (int w = 0; w < 7; w++) R1.t[w] = __ldg(d_shfl + (size_t)(off0 + 1) * 224 + 32 * w + lane);
+    }
     for (uint32_t p = threadIdx.x; p < pairs; p += blockDim.x) {
         const uint32_t q = ((p >> 5) << 6) | (p & 31);
         const uint32_t col = q & cmask, rest = q >> c;
@@ -207,8 +228,14 @@ __device__ __forceinline__ void reg_subpass2_pair(uint4 *s, int c, int g, int r_
                 const uint32_t *ct = ctab + (r - uf) * 224;
                 const uint32_t *dt = d_shfl + (size_t)(off + prefix) * 224;
                 ShflTab T;
+                if (kPairOffset && rr == 0 && B == 1) {
 #pragma unroll
-                for (int w = 0; w < 7; w++) T.t[w] = ct[32 * w + lane] ^ __ldg(dt + 32 * w + lane);
+                    for (int w = 0; w < 7; w++) T.t[w] = T0.t[w] ^ R1.t[w];
+                } else {
+#pragma unroll
+                    for (int w = 0; w < 7; w++) T.t[w] = ct[32 * w + lane] ^ __ldg(dt + 32 * w + lane);
+                    if (kPairOffset && rr == 0) T0 = T;
+                }
 #pragma unroll
                 for (int h = 0; h < 2; h++)
 #pragma unroll
