@@ -675,6 +675,12 @@ int gf2x_mul(const uint64_t *a, uint64_t na_bits, const uint64_t *b, uint64_t nb
     }
 }
 
+// Pieces of the product copied back while the rest is computed: the copy of
+// piece i starts as soon as the recombination has written it.
+#ifndef GF2X_HOST_PIECES
+#define GF2X_HOST_PIECES 4
+#endif
+
 int gf2x_mul_host(const uint64_t *a_host, uint64_t na_bits, const uint64_t *b_host,
                   uint64_t nb_bits, uint64_t *out_host, gf2x_stream_t stream) {
     try {
@@ -701,7 +707,7 @@ int gf2x_mul_host(const uint64_t *a_host, uint64_t na_bits, const uint64_t *b_ho
         // transformed on s; the product path waits for it before Split(b).
         // The output is written in pieces, each copied back on the copy
         // stream while the next one is computed.
-        constexpr int kPieces = 4;
+        constexpr int kPieces = GF2X_HOST_PIECES;
         cudaEvent_t ev[kPieces + 3] = {};
         bool ev_ok = true;
         for (auto &e : ev) ev_ok = ev_ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;

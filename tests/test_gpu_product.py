@@ -243,3 +243,25 @@ def test_basis_cvt_takes_grouped_passes(log_bits):
     assert st["ibasis_cvt"][1] <= 8, st["ibasis_cvt"]
     if log_bits <= 20:
         assert np.array_equal(got, P.mul(a, n, b, n))
+
+
+def test_plain_launches_without_programmatic_dependence():
+    # the product path's kernels are launched with programmatic dependent
+    # launch; GF2X_PDL=0 launches them in plain stream order: the same product
+    import os
+    import subprocess
+    import sys
+    na, nb = (1 << 20) + 3, (1 << 19) - 5
+    code = (
+        "import numpy as np, paper_1708_09746_gb300 as G, workloads as W\n"
+        "from oracle import product as P\n"
+        "import sys; sys.path.insert(0, 'tests')\n"
+        "from gpu_util import gpu_mul\n"
+        "a, b = W.operand_pair(99, %d, %d)\n"
+        "assert np.array_equal(gpu_mul(a, %d, b, %d), P.mul(a, %d, b, %d))\n"
+        "print('ok')\n" % (na, nb, na, nb, na, nb))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, GF2X_PDL="0")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stderr[-2000:]
