@@ -205,7 +205,8 @@ GF2X_API int gf2x_tune_load(const char *path);
  * enqueued on `stream`.  The arrays a, na_bits, b, nb_bits, out are HOST
  * arrays of `count` entries; a[i], b[i], out[i] are device pointers.  Plans
  * per size are cached and reused; workspaces come from one pooled device
- * allocation.  Asynchronous. */
+ * allocation.  The shape groups run on eight library-owned streams forked
+ * from `stream` and joined back into it.  Asynchronous. */
 GF2X_API int gf2x_mul_batched(int count, const uint64_t *const *a,
                      const uint64_t *na_bits, const uint64_t *const *b,
                      const uint64_t *nb_bits, uint64_t *const *out,

@@ -145,33 +145,6 @@ void fill_descs(const gf2x_batch *B, const uint64_t *const *a, const uint64_t *c
     }
 }
 
-// Every chunk, one after another, on s (workspace reused).
-int enqueue_chunks(const gf2x_batch *B, const OperandDesc *da, const OperandDesc *db,
-                   const OutputDesc *dout, void *ws, cudaStream_t s, StageHook *hook, int *st) {
-    const DevTables *T;
-    int rc = api::tables(&T);
-    if (rc) return rc;
-    if (!st) return GF2X_ECUDA;
-    const OperandDesc none_in{nullptr, 0, 0};
-    const OutputDesc none_out{nullptr, 0, 0};
-    for (const auto &ch : B->chunks) {
-        if (!ch.plan) {
-            launch_mul_small_many(da + ch.first, db + ch.first, dout + ch.first, ch.count,
-                                  ch.max_out_words, s);
-            if (hook) {
-                hook->begin(ST_OUT);
-                hook->end(1);
-            }
-            continue;
-        }
-        rc = plan_run_batch(ch.plan.get(), ch.count, da + ch.first, db + ch.first, dout + ch.first,
-                            none_in, none_in, none_out, ch.max_out_words, ws, ch.plan->ws_bytes, s,
-                            T, st, hook);
-        if (rc) return GF2X_ECUDA;
-    }
-    return GF2X_OK;
-}
-
 // Device work of a chunk, for balancing the branches: products times
 // N log2 N of their transforms (direct products: their output words).
 double chunk_cost(const gf2x_batch::Chunk &ch) {
@@ -229,6 +202,30 @@ int enqueue_branches(gf2x_batch *B, cudaStream_t s) {
     return GF2X_OK;
 }
 
+// Branch streams of one-shot batches (gf2x_mul_batched): created once per
+// device and reused by every call.
+int branch_streams(cudaStream_t (&out)[kBatchBranches]) {
+    static std::mutex mu;
+    static std::map<int, std::vector<cudaStream_t>> pool;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return GF2X_ECUDA;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    std::vector<cudaStream_t> &v = pool[dev];
+    while ((int)v.size() < kBatchBranches) {
+        cudaStream_t x = nullptr;
+        if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return GF2X_ECUDA;
+        }
+        v.push_back(x);
+    }
+    for (int k = 0; k < kBatchBranches; k++) out[k] = v[k];
+    return GF2X_OK;
+}
+
 int check_all(int count, const uint64_t *const *a, const uint64_t *na_bits,
               const uint64_t *const *b, const uint64_t *nb_bits, uint64_t *const *out) {
     for (int i = 0; i < count; i++) {
@@ -254,17 +251,20 @@ int gf2x_mul_batched(int count, const uint64_t *const *a, const uint64_t *na_bit
         gf2x_batch B;
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
-        if ((rc = batch_build(&B, count, na_bits, nb_bits, free_b / 2, 1))) return rc;
+        if ((rc = batch_build(&B, count, na_bits, nb_bits, free_b / 2, kBatchBranches))) return rc;
         if (B.order.empty()) return GF2X_OK;
         cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
         const size_t n = B.order.size();
         std::vector<OperandDesc> ha(n), hb(n);
         std::vector<OutputDesc> ho(n);
         fill_descs(&B, a, b, out, ha.data(), hb.data(), ho.data());
+        if ((rc = branch_streams(B.branch))) return rc;
         char *mem = nullptr;
         const size_t dbytes = n * (2 * sizeof(OperandDesc) + sizeof(OutputDesc));
         const size_t ws_off = (dbytes + 255) & ~(size_t)255;
-        if ((rc = api::ws_alloc(reinterpret_cast<void **>(&mem), ws_off + B.ws_bytes, s))) return rc;
+        if ((rc = api::ws_alloc(reinterpret_cast<void **>(&mem),
+                                ws_off + kBatchBranches * branch_stride(&B), s)))
+            return rc;
         OperandDesc *da = reinterpret_cast<OperandDesc *>(mem);
         OperandDesc *db = da + n;
         OutputDesc *dout = reinterpret_cast<OutputDesc *>(db + n);
@@ -272,8 +272,19 @@ int gf2x_mul_batched(int count, const uint64_t *const *a, const uint64_t *na_bit
         cudaMemcpyAsync(da, ha.data(), n * sizeof(OperandDesc), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(db, hb.data(), n * sizeof(OperandDesc), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(dout, ho.data(), n * sizeof(OutputDesc), cudaMemcpyHostToDevice, s);
-        std::unique_ptr<StageHook> tm(api::new_timer(s));
-        rc = enqueue_chunks(&B, da, db, dout, mem + ws_off, s, tm.get(), api::stream_status(s));
+        // the groups on the branch streams, forked from s and joined back into it
+        bool ev_ok = cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; ev_ok && k < kBatchBranches; k++)
+            ev_ok = cudaEventCreateWithFlags(&B.join[k], cudaEventDisableTiming) == cudaSuccess;
+        B.ws = mem + ws_off;
+        B.d_a = da;
+        B.d_b = db;
+        B.d_out = dout;
+        B.st = api::stream_status(s);
+        rc = !ev_ok ? GF2X_ECUDA : (!B.st ? GF2X_ECUDA : enqueue_branches(&B, s));
+        if (B.fork) cudaEventDestroy(B.fork);
+        for (int k = 0; k < kBatchBranches; k++)
+            if (B.join[k]) cudaEventDestroy(B.join[k]);
         api::ws_free(mem, s);
         if (rc == GF2X_OK && cudaGetLastError() != cudaSuccess) rc = GF2X_ECUDA;
         return rc;
