@@ -215,8 +215,9 @@ GF2X_API int gf2x_mul_batched(int count, const uint64_t *const *a,
 /* A reusable batch: the size list fixed at creation, the products grouped by
  * transform shape (log2 N, log2 Pa, log2 Pb) so that each group is one launch
  * per kernel, a device workspace of about mem_budget_bytes (0 = 4 GiB) shared
- * by eight graph branches (a group that does not fit a branch's share runs in
- * chunks; at least one product's workspace per branch) and, after the first
+ * by up to eight graph branches (a group that does not fit a branch's share
+ * runs in chunks; at least one product's workspace per branch, and fewer
+ * branches where the budget holds fewer such workspaces) and, after the first
  * execution, a CUDA graph of the whole batch that later executions replay: it
  * forks into the eight branches, which take the groups (largest first, each to
  * the least loaded branch) side by side, and joins them.  Host arrays of

@@ -51,7 +51,9 @@ struct gf2x_batch {
     std::vector<int> order;  // grouped order -> product index
     std::vector<Chunk> chunks;
     size_t ws_bytes = 0;  // per branch, shared by its chunks (run one after another)
-    void *ws = nullptr;   // kBatchBranches regions of ws_bytes (rounded to 256)
+    int nbr = 1;          // branches used: at most kBatchBranches, fewer where the
+                          // budget holds fewer branch workspaces
+    void *ws = nullptr;   // nbr regions of ws_bytes (rounded to 256)
     cudaStream_t branch[kBatchBranches] = {};
     cudaEvent_t fork = nullptr, join[kBatchBranches] = {};
     OperandDesc *d_a = nullptr, *d_b = nullptr;
@@ -98,7 +100,12 @@ int batch_build(gf2x_batch *B, int count, const uint64_t *na_bits, const uint64_
         max_one = std::max(max_one, p->ws_bytes);
         max_group_bytes = std::max(max_group_bytes, p->ws_bytes * kv.second.size());
     }
-    B->ws_bytes = std::max(max_one, std::min(max_group_bytes, mem_budget / std::max(1, branches)));
+    branches = std::max(1, branches);
+    B->ws_bytes = std::max(max_one, std::min(max_group_bytes, mem_budget / branches));
+    // a product whose workspace alone exceeds a branch's share: fewer branches
+    // (at least one), so that the batch stays within its budget where it can
+    B->nbr = (int)std::max<size_t>(
+        1, std::min<size_t>(branches, mem_budget / std::max<size_t>(1, B->ws_bytes)));
     for (auto &kv : groups) {
         std::shared_ptr<gf2x_plan> p;
         api::plan_for(B->na[kv.second[0]], B->nb[kv.second[0]], &p);
@@ -169,17 +176,18 @@ int enqueue_branches(gf2x_batch *B, cudaStream_t s) {
     std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
         return chunk_cost(B->chunks[x]) > chunk_cost(B->chunks[y]);
     });
+    const int nbr = std::max(1, std::min(B->nbr, kBatchBranches));
     double load[kBatchBranches] = {};
     std::vector<int> to(B->chunks.size(), 0);
     for (int c : ord) {
         int k = 0;
-        for (int q = 1; q < kBatchBranches; q++)
+        for (int q = 1; q < nbr; q++)
             if (load[q] < load[k]) k = q;
         to[c] = k;
         load[k] += chunk_cost(B->chunks[c]);
     }
     if (cudaEventRecord(B->fork, s) != cudaSuccess) return GF2X_ECUDA;
-    for (int k = 0; k < kBatchBranches; k++)
+    for (int k = 0; k < nbr; k++)
         if (cudaStreamWaitEvent(B->branch[k], B->fork, 0) != cudaSuccess) return GF2X_ECUDA;
     for (size_t c = 0; c < B->chunks.size(); c++) {
         const auto &ch = B->chunks[c];
@@ -195,7 +203,7 @@ int enqueue_branches(gf2x_batch *B, cudaStream_t s) {
                            ch.plan->ws_bytes, bs, T, B->st, nullptr))
             return GF2X_ECUDA;
     }
-    for (int k = 0; k < kBatchBranches; k++) {
+    for (int k = 0; k < nbr; k++) {
         if (cudaEventRecord(B->join[k], B->branch[k]) != cudaSuccess) return GF2X_ECUDA;
         if (cudaStreamWaitEvent(s, B->join[k], 0) != cudaSuccess) return GF2X_ECUDA;
     }
@@ -263,7 +271,7 @@ int gf2x_mul_batched(int count, const uint64_t *const *a, const uint64_t *na_bit
         const size_t dbytes = n * (2 * sizeof(OperandDesc) + sizeof(OutputDesc));
         const size_t ws_off = (dbytes + 255) & ~(size_t)255;
         if ((rc = api::ws_alloc(reinterpret_cast<void **>(&mem),
-                                ws_off + kBatchBranches * branch_stride(&B), s)))
+                                ws_off + (size_t)B.nbr * branch_stride(&B), s)))
             return rc;
         OperandDesc *da = reinterpret_cast<OperandDesc *>(mem);
         OperandDesc *db = da + n;
@@ -310,7 +318,7 @@ int gf2x_batch_create(int count, const uint64_t *na_bits, const uint64_t *nb_bit
         int rc = batch_build(B.get(), count, na_bits, nb_bits, mem_budget_bytes, kBatchBranches);
         if (rc) return rc;
         const size_t n = std::max<size_t>(1, B->order.size());
-        bool ok = cudaMalloc(&B->ws, kBatchBranches * std::max<size_t>(256, branch_stride(B.get()))) ==
+        bool ok = cudaMalloc(&B->ws, (size_t)B->nbr * std::max<size_t>(256, branch_stride(B.get()))) ==
                       cudaSuccess &&
                   cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) == cudaSuccess &&
                   cudaMalloc(&B->d_a, n * sizeof(OperandDesc)) == cudaSuccess &&
@@ -344,7 +352,7 @@ int gf2x_batch_create(int count, const uint64_t *na_bits, const uint64_t *nb_bit
 
 int gf2x_batch_workspace_bytes(const gf2x_batch *B, size_t *bytes) {
     if (!B || !bytes) return GF2X_EINVAL;
-    *bytes = kBatchBranches * branch_stride(B);
+    *bytes = (size_t)B->nbr * branch_stride(B);
     return GF2X_OK;
 }
 
