@@ -555,7 +555,7 @@ def measure_serving(G, torch, W, dev, seconds):
     max_out = (1 << 21) + 2
     outs = torch.empty((ring, max_out), dtype=torch.int64, device=dev)
     res = {}
-    for label, slots, batch in (("continuous_batching", 8, 64), ("one_at_a_time", 1, 1)):
+    for label, slots, batch in (("continuous_batching", 16, 64), ("one_at_a_time", 1, 1)):
         sv = G.gf2x_server_create(16 << 30, slots, batch)
         try:
             tickets = []
@@ -582,7 +582,7 @@ def measure_serving(G, torch, W, dev, seconds):
     # per second show what each server can carry, not the offered load
     depth = 512
     sat = {}
-    for label, slots, batch in (("continuous_batching", 8, 64), ("one_at_a_time", 1, 1)):
+    for label, slots, batch in (("continuous_batching", 16, 64), ("one_at_a_time", 1, 1)):
         sv = G.gf2x_server_create(16 << 30, slots, batch)
         try:
             tickets = []
